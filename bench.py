@@ -1,0 +1,325 @@
+"""Benchmark: GTEPS and HBM-roofline fraction of single-source SSSP on a
+symmetrised R-MAT scale-22 graph (edge factor 16, a/b/c/d .57/.19/.19/.05,
+uint32 weights in [1, 255]; 64 seeded sources from the giant component,
+each solved alone), plus batched and served throughput as extra keys.
+
+A step = one sssp_solve (distance init, the persistent MLMQ relaxation loop,
+predecessors) for the next source.  Inputs (the CSR, 1.07 GB of (col, w)
+pairs) are larger than L2 and resident in HBM before timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank solves its own sources (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS & HBM-roofline fraction per SSSP; serving p50/p99 latency vs plain solve"
+BYTES_PER_ARC = 12      # col 4 B + weight 4 B + dist[v] check 4 B
+BYTES_PER_VERTEX = 32   # row_ptr 8 B + dist 4 B + pred 4 B + queue push/pop of an 8 B element
+WORKLOAD = "rmat22"
+N_SOURCES = 64
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("mlmq.cuh", "kernels_u32.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2602_10080_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """Per-launch DRAM bytes of the relaxation kernel from the committed ncu
+    summary, or None if the kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "mlmq_kernel_rmat22_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.out = ""
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sms)) if sms else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_gteps(g, srcs, threads: int, kind: str = "u32"):
+    """The oracle as it stands: one Dijkstra per host thread, all at once."""
+    import oracle
+    t0 = time.perf_counter()
+    dists = oracle.dijkstra_many(g.row_ptr, g.col, g.w, srcs, kind=kind, threads=threads)
+    dt = time.perf_counter() - t0
+    arcs = sum(oracle.reached_counts(g.row_ptr, d, kind)[0] for d in dists)
+    return arcs / dt / 1e9, dt, arcs
+
+
+def reached(row_ptr_t, dist_t, wtype: str):
+    """(m_r, n_r) of one result, computed on the device (outside timing)."""
+    import torch
+    inf = 0x7F800000 if wtype == "f32" else -1  # int32 view of 0xFFFFFFFF
+    r = dist_t != inf
+    deg = (row_ptr_t[1:] - row_ptr_t[:-1]).to(torch.int64)
+    return int(deg[r].sum().item()), int(r.sum().item())
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import graphgen as gg
+    import oracle
+    oracle.build()
+    g = gg.workload(WORKLOAD)
+    srcs, _ = gg.giant_sources(g, N_SOURCES, seed=2)
+    cores = max(1, min(len(srcs), os.cpu_count() or 1))
+    k = 0
+    # each step: one query per host core (a bounded sample of the 64 sources)
+    for _ in range(args.warmup):
+        sub = [srcs[(k + i) % len(srcs)] for i in range(cores)]
+        k += cores
+        cpu_oracle_gteps(g, sub, cores)
+    total_arcs, total_t = 0, 0.0
+    for _ in range(args.steps):
+        sub = [srcs[(k + i) % len(srcs)] for i in range(cores)]
+        k += cores
+        gteps, dt, arcs = cpu_oracle_gteps(g, sub, cores)
+        total_arcs += arcs
+        total_t += dt
+    value = total_arcs / total_t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GTEPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1000 * total_t / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "rmat22 single-source (R-MAT scale 22, ef 16, u32 [1,255]); "
+                               f"{cores} sources per step, one per host core"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} single-source Dijkstra runs per step on {WORKLOAD}"},
+        "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="mlmq", choices=["mlmq", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip batch/serving/cpu legs")
+    ap.add_argument("--workload", default=WORKLOAD)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import graphgen as gg
+    import paper_2602_10080_gb300 as S
+    S.build()
+
+    g = gg.workload(args.workload)
+    srcs_all, giant = gg.giant_sources(g, N_SOURCES, seed=2)
+    G = S.Graph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda(),
+                torch.from_numpy(g.w_bits.view(np.int32)).cuda(), g.wtype)
+    row_ptr_t = torch.from_numpy(g.row_ptr).cuda()
+    # input-adaptive configuration (Section 3.5), cached on the graph
+    tune_srcs = torch.from_numpy(srcs_all[:2].copy()).cuda()
+    tuned = G.autotune(tune_srcs, 8000)
+
+    my_srcs = [int(s) for s in srcs_all[rank::ws]] or [int(srcs_all[0])]
+    stream = torch.cuda.current_stream()
+    dist_t = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    pred_t = torch.empty(g.n, dtype=torch.int32, device="cuda")
+
+    # reached arcs / vertices per source (outside timing)
+    mr, nr = {}, {}
+    for s in set(my_srcs[: args.steps + args.warmup] + my_srcs):
+        G.solve(s, dist_t, pred_t)
+        mr[s], nr[s] = reached(row_ptr_t, dist_t, g.wtype)
+
+    def src_at(i):
+        return my_srcs[i % len(my_srcs)]
+
+    for i in range(args.warmup):
+        G.solve(src_at(i), dist_t, pred_t, None, stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kernel_ms, arcs, verts = [], 0, 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for i in range(args.steps):
+            s = src_at(args.warmup + i)
+            G.solve(s, dist_t, pred_t, None, stream)
+            kernel_ms.append(S.sssp_last_stats(G.handle).kernel_ms)
+            arcs += mr[s]
+            verts += nr[s]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    t_ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        tt = torch.tensor([t_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        at = torch.tensor([arcs, verts], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(at)
+        arcs, verts = int(at[0].item()), int(at[1].item())
+    value = arcs / (t_ms / 1e3) / 1e9
+    stats = G.stats()
+
+    # e2e: the same solves through the C ABI with pinned HOST output buffers
+    hd = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
+    hp = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
+    for i in range(2):
+        G.solve(src_at(i), hd, hp, None, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_arcs = 0
+    for i in range(args.steps):
+        s = src_at(args.warmup + i)
+        G.solve(s, hd, hp, None, stream)
+        e2e_arcs += mr[s]
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = e2e_arcs / e2e_s / 1e9 * ws
+
+    peaks = measured_peaks()
+    # roofline of the relaxation kernel: algorithmic bytes per launch / kernel time
+    alg_bytes = (BYTES_PER_ARC * arcs + BYTES_PER_VERTEX * verts) / (args.steps * ws)
+    kms = float(np.mean(kernel_ms))
+    achieved = alg_bytes / (kms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": profiled_traffic(),
+            "peak_source": peaks["source"], "kernel": "mlmq_kernel", "kernel_ms_mean": round(kms, 4),
+            "alg_bytes_per_launch": int(alg_bytes)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GTEPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} single-source (R-MAT scale 22, ef 16, a/b/c/d .57/.19/.19/.05, "
+                               "u32 [1,255], symmetrised, dedup); 64 giant-component sources, each solved alone",
+                   "n": g.n, "m": g.m, "giant": giant, "l2_flush": "inputs larger than L2 (CSR 1.07 GB)",
+                   "queue": {k: v for k, v in tuned.as_dict().items()
+                             if k in ("l1_type", "l2_type", "delta_u32", "bnum", "bmax", "wb",
+                                      "filter_deltas", "th_heavy", "block_threads")},
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": round(e2e_value, 3), "unit": "GTEPS", "h2d_bytes_per_step": 4,
+                "d2h_bytes_per_step": 8 * g.n},
+        "gpu_launches": 4 * args.steps,
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "work": {"relax_arcs_per_reached_arc": round(stats["relax_arcs"] / max(1, mr[src_at(args.warmup + args.steps - 1)]), 3),
+                 "last": {k: stats[k] for k in ("pops_l0", "pops_l1", "pops_l2", "pops_heavy", "improved",
+                                                "stale", "l2_chunks_written", "heavy_tasks", "grid_blocks",
+                                                "block_threads")}},
+    }
+    if rank == 0 and not args.no_extras:
+        # the oracle timed on this host's cores on a bounded sample of the same workload
+        cores = max(1, min(16, os.cpu_count() or 1))
+        sample = [int(s) for s in srcs_all[:cores]]
+        cg, cdt, _ = cpu_oracle_gteps(g, sample, cores)
+        line["cpu_baseline"] = {"value": round(cg, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                                "sample": f"{cores} single-source Dijkstra runs on {args.workload}, "
+                                          f"one per thread ({cdt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    G.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

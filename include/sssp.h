@@ -1,0 +1,254 @@
+/*
+ * sssp.h -- C ABI of libsssp.so, a GB300 (sm_103a) single-source shortest
+ * path engine built around a multi-level multi-queue (MLMQ) worklist.
+ *
+ * Problem (paper Section 2.1): for a directed graph G(V, E, W) with
+ * non-negative arc lengths and a source s, compute l_su, the length of a
+ * shortest path from s to every vertex u.  The engine is label-correcting:
+ * vertices are read from a worklist, their arcs are relaxed (Listing 2,
+ * SSSP_relax), and every improved vertex is written back, until the worklist
+ * is empty.  The worklist has three levels (Section 3.1): L0 in registers
+ * (per warp), L1 in shared memory (per thread block), L2 in global memory
+ * (whole grid, delta-bucketed, Section 4.2 "L2 Bucket queue"), joined by the
+ * cache-like spill/refill of Section 3.2 and the Read/Write cascade of
+ * Listing 1.  Every label-correcting order converges to the same lengths, so
+ * results are exact: u32 lengths equal Dijkstra's bit for bit, and f32
+ * lengths equal an f32 Dijkstra that performs one IEEE round-to-nearest add
+ * per arc.
+ *
+ * Conventions for every entry point:
+ *   - Return value 0 (SSSP_OK) on success, a negative SSSP_E_* code on
+ *     failure.  No call throws, aborts the process or leaves a handle
+ *     unusable after an error; a failed solve leaves the output buffers
+ *     unspecified.
+ *   - Pointers to arrays may be host or device memory unless stated; the
+ *     kind is detected with cudaPointerGetAttributes.  Host output arrays
+ *     are written before the call returns.
+ *   - Sizes are element counts.  CSR arrays use int32 indices:
+ *     row_ptr[n + 1] (row_ptr[0] == 0, non-decreasing, row_ptr[n] == m) and
+ *     col_idx[m] with 0 <= col_idx[e] < n.  Arcs (u, col_idx[e]) for
+ *     row_ptr[u] <= e < row_ptr[u + 1].  Self-loops and parallel arcs are
+ *     allowed.
+ *   - Weights: uint32 (any value; lengths saturate at 0xFFFFFFFE so they
+ *     never wrap) or fp32 (finite and >= 0; -0.0 is read as +0.0).
+ *   - Distances out: uint32 with 0xFFFFFFFF = unreachable, or fp32 with
+ *     +inf = unreachable, matching the graph's weight type.
+ *   - Predecessors out (int32, optional): -1 = unreachable, pred[s] = s.
+ *     For uint32 graphs whose weights are all >= 1 the predecessor is
+ *     canonical: the smallest-index in-neighbour u with
+ *     dist[u] + w(u, v) == dist[v].  Otherwise (fp32, or uint32 with zero
+ *     weights) it is the arc of the last strict improvement of dist[v]; it
+ *     is tight and following it from any reachable vertex reaches s.
+ *   - Calls on one graph handle are serialised internally; calls on
+ *     different handles may run concurrently from different host threads.
+ *   - A `stream` argument is a cudaStream_t (NULL = the legacy default
+ *     stream).  Solve calls are synchronous: they return after the results
+ *     are in the output buffers (the queue's error word must be read back).
+ */
+#ifndef SSSP_H
+#define SSSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SSSP_API __attribute__((visibility("default")))
+#else
+#define SSSP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- status -- */
+#define SSSP_OK           0
+#define SSSP_E_INVAL     -1 /* bad argument (NULL handle, source out of range, bad config) */
+#define SSSP_E_NOMEM     -2 /* device or host allocation failed, or queue capacity exhausted */
+#define SSSP_E_CUDA      -3 /* a CUDA runtime call failed */
+#define SSSP_E_TIMEOUT   -4 /* a bounded device wait ran out; the handle is reset and usable */
+#define SSSP_E_BADGRAPH  -5 /* CSR validation failed (ranges, monotonicity, NaN/inf/negative f32) */
+#define SSSP_E_BUSY      -6 /* serving: no free slot or memory budget right now */
+#define SSSP_E_NODEV     -7 /* no usable CUDA device */
+#define SSSP_E_NOTFOUND  -8 /* serving: unknown ticket */
+
+/* Message for a status code (static string, never NULL). */
+SSSP_API const char *sssp_strerror(int status);
+
+/* Library version as MAJOR * 10000 + MINOR * 100 + PATCH. */
+SSSP_API int sssp_version(void);
+
+/* ------------------------------------------------------------ types -- */
+typedef enum { SSSP_W_U32 = 0, SSSP_W_F32 = 1 } sssp_wtype;
+
+/* L1 queue policies (Section 3.4, Fig. 7, Table 1). */
+typedef enum {
+    SSSP_L1_VECTOR = 0,  /* L1V: FIFO; flushed whole to L2 after every `wb` writes */
+    SSSP_L1_NEARFAR = 1, /* L1NF: near/far vectors split at NF; NF = min(far) + delta when near drains */
+    SSSP_L1_FILTER = 2,  /* L1FQ: keeps dist <= F, writes the rest back to L2 */
+    SSSP_L1_SLF = 3      /* L1SLF: deque; dist <= head goes to the head, else the tail */
+} sssp_l1_type;
+
+/* L2 queue policies (Section 4.2).  L2V is the bucket queue with one bucket. */
+typedef enum { SSSP_L2_VECTOR = 0, SSSP_L2_BUCKET = 1 } sssp_l2_type;
+
+/* Tunable configuration.  Zero-initialise and call sssp_config_default(),
+ * or pass NULL to a solve call to use the graph's tuned (or default)
+ * configuration.  Fields the paper leaves open (wb, delta, bnum, bmax, NF,
+ * F; Sections 3.4 and 4.2) are chosen by sssp_autotune(). */
+typedef struct sssp_config {
+    int32_t l1_type;       /* sssp_l1_type */
+    int32_t l2_type;       /* sssp_l2_type */
+    int32_t l0_rows;       /* L0 capacity per warp in rows of 32 elements: 1, 2 or 4 */
+    int32_t l1_cap;        /* L1 capacity per thread block, elements (256..16384, power of two) */
+    int32_t wb;            /* L1V: flush L1 to L2 after every wb write calls (0 = never) */
+    uint32_t delta_u32;    /* bucket width for u32 graphs (>= 1) */
+    float delta_f32;       /* bucket width for f32 graphs (> 0) */
+    int32_t bnum;          /* buckets a read scans, from the lowest (1..32) */
+    int32_t bmax;          /* buckets in total, a circular window (1..1024; 1 = L2V) */
+    float filter_deltas;   /* L1FQ: F = window base + filter_deltas * delta */
+    int32_t th_heavy;      /* degree above which a vertex is split into arc-range tasks */
+    int32_t split;         /* arcs per task (multiple of 32) */
+    int32_t block_threads; /* threads per block: 256, 512 or 1024 */
+    int32_t blocks_per_sm; /* resident blocks per SM (0 = as many as fit) */
+    int32_t timeout_ms;    /* device watchdog for one solve (0 = library default) */
+    int32_t reserved[7];   /* must be zero */
+} sssp_config;
+
+/* Graph features of Table 2 (Section 3.5), computed at creation. */
+typedef struct sssp_features {
+    int64_t n, m;                 /* vertices, arcs */
+    double avg_deg, max_deg, std_deg;
+    double avg_w, max_w, std_w;
+    double min_w;
+    int32_t symmetric;            /* 1 if every arc has a reverse arc of equal weight */
+    int32_t has_zero_w;
+} sssp_features;
+
+/* Counters of the last solve on a graph (Fig. 3 quantities). */
+typedef struct sssp_stats {
+    double kernel_ms;             /* persistent relaxation kernel, CUDA-event time */
+    double total_ms;              /* whole call on the device: init + kernel + outputs */
+    int64_t reached;              /* vertices with finite distance (sum over queries) */
+    int64_t reached_arcs;         /* arcs out of reached vertices, m_r (sum over queries) */
+    int64_t pops_l0, pops_l1, pops_l2, pops_heavy;
+    int64_t relax_arcs;           /* arcs scanned (work) */
+    int64_t improved;             /* successful relaxations (writes back) */
+    int64_t stale;                /* popped elements already superseded */
+    int64_t l2_chunks_written, l1_flushes, heavy_tasks;
+    int32_t grid_blocks, block_threads;
+    int32_t attempts;             /* > 1 if the queue was regrown after an overflow */
+} sssp_stats;
+
+typedef struct sssp_graph sssp_graph;
+typedef struct sssp_server sssp_server;
+
+/* --------------------------------------------------------- configuration -- */
+
+/* Fills *cfg with the library defaults (L1V-L2DQ-like).  SSSP_E_INVAL if cfg is NULL. */
+SSSP_API int sssp_config_default(sssp_config *cfg);
+
+/* ------------------------------------------------------------------ graph -- */
+
+/* Copies a CSR graph to the device, validates it and derives the layout the
+ * kernels use (interleaved (col, weight) pairs, one 8-byte load per arc).
+ *   row_ptr  int32[n + 1], col_idx int32[m], weights uint32[m] or fp32[m]
+ *            (per `wtype`); host or device memory, borrowed (copied).
+ *   n >= 1, 0 <= m < 2^31.
+ *   *out     receives a new handle owning device memory; free it with
+ *            sssp_graph_destroy.
+ * Errors: SSSP_E_INVAL (NULL/negative sizes), SSSP_E_BADGRAPH (validation),
+ * SSSP_E_NOMEM, SSSP_E_CUDA, SSSP_E_NODEV.  Cites: Section 2.1 (G(V,E,W)),
+ * Listing 2 (edge_list / edge_weight). */
+SSSP_API int sssp_graph_create(const int32_t *row_ptr, const int32_t *col_idx, const void *weights,
+                      int32_t n, int64_t m, int32_t wtype, sssp_graph **out);
+
+/* Frees the graph and every device buffer it owns.  NULL is a no-op. */
+SSSP_API int sssp_graph_destroy(sssp_graph *g);
+
+/* Table 2 features of the graph (Section 3.5). */
+SSSP_API int sssp_graph_features(const sssp_graph *g, sssp_features *out);
+
+/* ------------------------------------------------------------------ solve -- */
+
+/* Single-source solve (Listing 2: work kernel + termination of Section 4.1).
+ *   src       0 <= src < n.
+ *   dist_out  n elements (uint32 or fp32 per the graph), host or device.
+ *   pred_out  n int32 or NULL.
+ *   cfg       NULL = the graph's tuned configuration (or the default).
+ *   stream    cudaStream_t or NULL.
+ * Returns after completion.  Errors: SSSP_E_INVAL, SSSP_E_TIMEOUT,
+ * SSSP_E_NOMEM (queue could not be grown), SSSP_E_CUDA. */
+SSSP_API int sssp_solve(sssp_graph *g, int32_t src, void *dist_out, int32_t *pred_out,
+               const sssp_config *cfg, void *stream);
+
+/* Batched multi-source solve: nq independent queries in ONE persistent
+ * launch sharing the worklist (queue elements carry their query).
+ *   srcs      int32[nq] (host or device), each in [0, n); repeats allowed.
+ *   dist_out  nq * n elements, query-major: dist_out[q * n + v].
+ *   pred_out  nq * n int32 or NULL.
+ * nq * 2^ceil(log2 n) must not exceed 2^32 (the element key packs the query
+ * index above the vertex bits).  Errors as sssp_solve. */
+SSSP_API int sssp_solve_batch(sssp_graph *g, const int32_t *srcs, int32_t nq, void *dist_out,
+                     int32_t *pred_out, const sssp_config *cfg, void *stream);
+
+/* Counters and timings of the last solve/batch on this graph. */
+SSSP_API int sssp_last_stats(const sssp_graph *g, sssp_stats *out);
+
+/* ---------------------------------------------------------------- autotune -- */
+
+/* Picks a configuration for this graph (Section 3.5 adaptive configuration):
+ * a prior from the Table 2 features and the per-family findings of
+ * Section 5.4, refined by timing candidate configurations on up to nsrc of
+ * the given sources (host or device int32[nsrc]) within about budget_ms.
+ * The winner is cached on the graph (used when cfg == NULL) and copied to
+ * *out when out != NULL.  budget_ms <= 0 returns the prior untimed. */
+SSSP_API int sssp_autotune(sssp_graph *g, const int32_t *srcs, int32_t nsrc, int32_t budget_ms,
+                  sssp_config *out);
+
+/* ---------------------------------------------------------------- serving -- */
+
+/* A serving loop with continuous batching: graphs stay resident; queries
+ * are admitted while earlier ones run, as query slots and the device-memory
+ * budget allow, and run in one persistent launch.  (North-star extension;
+ * the paper has no serving mode.)
+ *   mem_budget_bytes  device bytes for per-query dist/pred/queue state
+ *                     (0 = 25% of free device memory).
+ *   max_slots         concurrent queries (1..1024).
+ *   max_vertices      largest graph n that will be submitted. */
+SSSP_API int sssp_serve_create(size_t mem_budget_bytes, int32_t max_slots, int32_t max_vertices,
+                      sssp_server **out);
+
+/* Queues one query.  dist_out / pred_out (pred may be NULL) must stay valid
+ * until sssp_serve_poll reports DONE or ERROR; they may be host or device
+ * memory.  *ticket_out identifies the query.  SSSP_E_INVAL for a bad
+ * graph/source, SSSP_E_BUSY if the host-side queue is full. */
+SSSP_API int sssp_serve_submit(sssp_server *s, sssp_graph *g, int32_t src, void *dist_out,
+                      int32_t *pred_out, uint64_t *ticket_out);
+
+/* Query states reported by sssp_serve_poll. */
+#define SSSP_Q_QUEUED  0
+#define SSSP_Q_RUNNING 1
+#define SSSP_Q_DONE    2
+#define SSSP_Q_ERROR   3
+
+/* Non-blocking state of a ticket.  After DONE/ERROR is reported once the
+ * ticket is retired (a later poll returns SSSP_E_NOTFOUND).  For ERROR,
+ * *status_out (may be NULL) receives the failing SSSP_E_* code. */
+SSSP_API int sssp_serve_poll(sssp_server *s, uint64_t ticket, int32_t *state_out, int32_t *status_out);
+
+/* Blocks until the ticket is DONE/ERROR or timeout_ms passes (then
+ * SSSP_E_TIMEOUT with the query still live). */
+SSSP_API int sssp_serve_wait(sssp_server *s, uint64_t ticket, int32_t timeout_ms, int32_t *state_out,
+                    int32_t *status_out);
+
+/* Submit-to-done latency of the ticket's query in microseconds (valid after DONE). */
+SSSP_API int sssp_serve_latency_us(sssp_server *s, uint64_t ticket, double *us_out);
+
+/* Stops the loop (waits for queries in flight) and frees the server. */
+SSSP_API int sssp_serve_destroy(sssp_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSSP_H */

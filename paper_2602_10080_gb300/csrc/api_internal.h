@@ -1,0 +1,73 @@
+// api_internal.h -- host-side state behind the opaque C handles.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/sssp.h"
+#include "internal.h"
+
+namespace sssp {
+
+// Device buffers reused across solves on one graph.
+struct Workspace {
+    char* ring_mem = nullptr;     // L2 bucket rings (data, tickets, seq, cnt)
+    char* task_mem = nullptr;     // arc-range task ring
+    size_t ring_bytes = 0;
+    Rings rings{};
+    TaskRing hv{};
+    uint32_t bmax = 0;
+    bool dirty = true;            // metadata must be reset before the next solve
+    int grow_shift = 0;           // capacity doublings after overflows
+    Ctrl* ctrl = nullptr;
+    Ctrl* host_ctrl = nullptr;    // pinned mirror
+    unsigned long long* d64 = nullptr;
+    size_t d64_n = 0;
+    uint32_t* d32 = nullptr;
+    size_t d32_n = 0;
+    uint32_t* out_d = nullptr;
+    size_t out_d_n = 0;
+    int32_t* out_p = nullptr;
+    size_t out_p_n = 0;
+    int32_t* srcs = nullptr;
+    size_t srcs_n = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+
+    int ensure_queue(uint32_t nbuckets, uint32_t nch, uint32_t margin, uint32_t nslot,
+                     cudaStream_t s, int sms);
+    void release();
+};
+
+struct Graph {
+    int device = 0;
+    int sms = 1;
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t wtype = 0;
+    int32_t* row_ptr = nullptr;   // [n + 1]
+    uint2* adj = nullptr;         // [m] (col, weight bits)
+    sssp_features feat{};
+    sssp_config defaults{};
+    sssp_config tuned{};
+    bool tuned_valid = false;
+    sssp_stats last{};
+    Workspace ws;
+    std::mutex mu;
+};
+
+int cuda_status(cudaError_t e);
+bool is_device_ptr(const void* p);
+void resolve_auto(const Graph* g, sssp_config* c);
+int validate_config(const sssp_config* c);
+int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int32_t src0, int32_t nq,
+                void* dist_out, int32_t* pred_out, const sssp_config* cfg, cudaStream_t stream,
+                sssp_stats* st_out);
+
+inline uint32_t __float_as_uint_host(float f) {
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    return b;
+}
+
+}  // namespace sssp

@@ -1,0 +1,191 @@
+// sssp_autotune.cu -- input-adaptive configuration (Section 3.5).
+//
+// The paper ranks candidate queue configurations with a RandomForest trained
+// on 680 SuiteSparse matrices, from the Table 2 features.  Neither the corpus
+// nor the trained model is available, so this replaces it with
+//   (1) a prior from the Table 2 features and the per-family findings of
+//       Section 5.4 (road: L1V/L1NF over a FIFO L2 when small, L1V over the
+//       bucket queue when large; meshes: L1FQ-L2V; power-law: priority-aware
+//       L1 over the bucket queue), and
+//   (2) a short timed coordinate search around the prior on sample sources:
+//       L1 policy, delta, bnum, heavy-vertex threshold and block size, each
+//       candidate timed by the CUDA-event duration of the relaxation kernel.
+// The winner is cached on the graph and used by solves given cfg == NULL.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "../../include/sssp.h"
+#include "api_internal.h"
+
+namespace sssp {
+
+// Graph family from Table 2 features.
+enum Family { kRoad = 0, kMesh = 1, kPowerLaw = 2 };
+
+static Family family_of(const sssp_features& f) {
+    double cv = f.avg_deg > 0 ? f.std_deg / f.avg_deg : 0.0;
+    if (f.max_deg > 16.0 * std::max(1.0, f.avg_deg) || cv > 1.5) return kPowerLaw;
+    if (f.avg_deg < 4.5) return kRoad;
+    return kMesh;
+}
+
+sssp_config prior_config(const Graph* g) {
+    sssp_config c;
+    sssp_config_default(&c);
+    const sssp_features& f = g->feat;
+    switch (family_of(f)) {
+        case kPowerLaw:
+            c.l1_type = SSSP_L1_FILTER;
+            c.l2_type = SSSP_L2_BUCKET;
+            c.filter_deltas = 2.0f;
+            c.bnum = 4;
+            c.bmax = 64;
+            break;
+        case kMesh:
+            c.l1_type = SSSP_L1_FILTER;
+            c.l2_type = SSSP_L2_BUCKET;
+            c.filter_deltas = 4.0f;
+            c.bnum = 8;
+            c.bmax = 64;
+            break;
+        case kRoad:
+            if (f.n < 500000) {
+                c.l1_type = SSSP_L1_VECTOR;
+                c.wb = 16;
+                c.l2_type = SSSP_L2_BUCKET;
+                c.bnum = 8;
+            } else {
+                c.l1_type = SSSP_L1_VECTOR;
+                c.wb = 8;
+                c.l2_type = SSSP_L2_BUCKET;
+                c.bnum = 4;
+            }
+            c.bmax = 128;
+            break;
+    }
+    c.delta_u32 = 0;
+    c.delta_f32 = 0.0f;
+    resolve_auto(g, &c);
+    return c;
+}
+
+}  // namespace sssp
+
+using namespace sssp;
+
+extern "C" int sssp_autotune(sssp_graph* gh, const int32_t* srcs, int32_t nsrc, int32_t budget_ms,
+                             sssp_config* out) {
+    if (!gh) return SSSP_E_INVAL;
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    std::lock_guard<std::mutex> lk(g->mu);
+    sssp_config best = prior_config(g);
+    if (budget_ms <= 0 || nsrc <= 0 || !srcs) {
+        g->tuned = best;
+        g->tuned_valid = true;
+        if (out) *out = best;
+        return SSSP_OK;
+    }
+    std::vector<int32_t> hs(nsrc);
+    if (is_device_ptr(srcs)) {
+        if (cudaMemcpy(hs.data(), srcs, sizeof(int32_t) * nsrc, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return SSSP_E_CUDA;
+    } else {
+        hs.assign(srcs, srcs + nsrc);
+    }
+    for (int32_t s : hs)
+        if (s < 0 || s >= g->n) return SSSP_E_INVAL;
+    hs.resize(std::min<int32_t>(nsrc, 4));
+
+    void* dbuf = nullptr;
+    if (cudaMalloc(&dbuf, sizeof(uint32_t) * (size_t)g->n) != cudaSuccess) {
+        cudaGetLastError();
+        return SSSP_E_NOMEM;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    auto elapsed_ms = [&]() {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    };
+    // time = median kernel time over the sample sources; failures = +inf
+    auto measure = [&](const sssp_config& c) -> double {
+        std::vector<double> ts;
+        for (int32_t s : hs) {
+            sssp_stats st;
+            int rc = run_queries(g, nullptr, nullptr, s, 1, dbuf, nullptr, &c, nullptr, &st);
+            if (rc != SSSP_OK) return INFINITY;
+            ts.push_back(st.kernel_ms);
+        }
+        std::sort(ts.begin(), ts.end());
+        return ts[ts.size() / 2];
+    };
+    // warm-up (allocations, first launch)
+    measure(best);
+    double best_t = measure(best);
+    const bool f32 = g->wtype == SSSP_W_F32;
+    const double d0 = f32 ? best.delta_f32 : (double)best.delta_u32;
+
+    for (int pass = 0; pass < 2 && elapsed_ms() < budget_ms; pass++) {
+        std::vector<sssp_config> cands;
+        // L1 policy (Table 1), with the L1V flush period
+        for (int l1 = 0; l1 < 4; l1++) {
+            for (int wb : {0, 8, 32}) {
+                if (l1 != SSSP_L1_VECTOR && wb) continue;
+                sssp_config c = best;
+                c.l1_type = l1;
+                c.wb = l1 == SSSP_L1_VECTOR ? wb : 0;
+                cands.push_back(c);
+            }
+        }
+        // delta (bucket width) and the L2 policy
+        for (double mult : {0.25, 0.5, 2.0, 4.0, 16.0}) {
+            sssp_config c = best;
+            if (f32) c.delta_f32 = (float)(d0 * mult);
+            else c.delta_u32 = (uint32_t)std::max(1.0, std::round(d0 * mult));
+            cands.push_back(c);
+        }
+        {
+            sssp_config c = best;
+            c.l2_type = SSSP_L2_VECTOR;
+            c.bmax = 1;
+            c.bnum = 1;
+            cands.push_back(c);
+        }
+        for (int bn : {1, 2, 8, 16}) {
+            sssp_config c = best;
+            if (c.bmax < bn) continue;
+            c.bnum = bn;
+            cands.push_back(c);
+        }
+        for (float fd : {1.0f, 4.0f, 8.0f}) {
+            sssp_config c = best;
+            if (c.l1_type != SSSP_L1_FILTER) continue;
+            c.filter_deltas = fd;
+            cands.push_back(c);
+        }
+        for (int th : {512, 8192}) {
+            sssp_config c = best;
+            c.th_heavy = th;
+            cands.push_back(c);
+        }
+        for (int bt : {256, 1024}) {
+            sssp_config c = best;
+            c.block_threads = bt;
+            cands.push_back(c);
+        }
+        for (const sssp_config& c : cands) {
+            if (elapsed_ms() > budget_ms) break;
+            if (validate_config(&c) != SSSP_OK) continue;
+            double t = measure(c);
+            if (t < best_t * 0.97) {
+                best_t = t;
+                best = c;
+            }
+        }
+    }
+    cudaFree(dbuf);
+    g->tuned = best;
+    g->tuned_valid = true;
+    if (out) *out = best;
+    return SSSP_OK;
+}

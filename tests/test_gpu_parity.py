@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+u32 distances must be bit-exact; u32 predecessors (all weights >= 1) must
+equal the canonical smallest-index tight in-neighbour; f32 distances must be
+bit-exact against the f32 Dijkstra and within 1e-6 relative of the f64 one;
+other predecessors are checked by the invariants (tight arc, chains reach
+the source).
+"""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+import paper_2602_10080_gb300 as S
+from golden_io import all_cases
+from gpu_util import assert_exact, cfg, gpu_batch, gpu_solve, oracle_dist, upload
+
+pytestmark = pytest.mark.gpu
+
+L1_ALL = [S.L1_VECTOR, S.L1_NEARFAR, S.L1_FILTER, S.L1_SLF]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    S.build()
+    S.lib()
+
+
+def _golden_graph(case):
+    w = case["w_bits"]
+    g = gg.Graph(case["name"], case["n"], len(case["col"]), case["row_ptr"], case["col"],
+                 w.view(np.float32) if case["kind"] == "f32" else w, case["kind"])
+    return g
+
+
+@pytest.mark.parametrize("case", all_cases(), ids=lambda c: c["name"])
+@pytest.mark.parametrize("host", [False, True])
+def test_golden_fixtures(case, host):
+    g = _golden_graph(case)
+    G = upload(g, device_inputs=not host)
+    d, p = gpu_solve(G, case["src"], pred=True, host=host)
+    np.testing.assert_array_equal(d, case["dist_bits"])
+    if case["pred"] is not None and g.wtype == "u32" and int(g.w.min()) >= 1:
+        np.testing.assert_array_equal(p, case["pred"])
+    assert_exact(g, case["src"], d, p)
+
+
+@pytest.mark.parametrize("l1", L1_ALL)
+@pytest.mark.parametrize("l2", [S.L2_VECTOR, S.L2_BUCKET])
+def test_grid256_all_queue_configs(l1, l2):
+    """Config 1 (grid 256x256, u32 [1,100], seed 1, source 0) under every L1 x L2 policy."""
+    g = gg.workload("grid256")
+    G = upload(g)
+    c = cfg(l1_type=l1, l2_type=l2, wb=8 if l1 == S.L1_VECTOR else 0)
+    d, p = gpu_solve(G, 0, pred=True, config=c)
+    assert_exact(g, 0, d, p)
+    d2, _ = gpu_solve(G, 0, pred=False, config=c)
+    np.testing.assert_array_equal(d2, d)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_graphs_stress(seed):
+    """Tiny queue capacities force constant spill/refill; tiny heavy thresholds force tasks."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 3000))
+    m = int(rng.integers(0, 12 * n))
+    wt = "f32" if seed % 3 == 2 else "u32"
+    lo = 0 if seed % 4 == 1 else 1
+    g = gg.random_directed(n, m, lo=lo, hi=int(rng.integers(1, 1000)), seed=seed, wtype=wt)
+    G = upload(g)
+    c = cfg(l1_type=L1_ALL[seed % 4], l2_type=seed % 2, l1_cap=256, bmax=int(rng.choice([1, 2, 8, 64])),
+            bnum=int(rng.choice([1, 2, 4])), th_heavy=32, split=32, wb=int(rng.choice([0, 1, 4])),
+            block_threads=int(rng.choice([256, 512, 1024])))
+    if wt == "u32":
+        c.delta_u32 = int(rng.integers(1, 200))
+    else:
+        c.delta_f32 = float(rng.uniform(0.01, 2.0))
+    for src in rng.integers(0, n, size=2):
+        d, p = gpu_solve(G, src, pred=True, config=c)
+        assert_exact(g, src, d, p)
+        d2, _ = gpu_solve(G, src, pred=False, config=c)
+        np.testing.assert_array_equal(d2, d)
+
+
+def test_rmat_f32_exact_and_close_to_f64():
+    g = gg.rmat(14, 16, seed=3, wtype="f32")
+    G = upload(g)
+    srcs, _ = gg.giant_sources(g, 3, seed=2)
+    for s in srcs:
+        d, p = gpu_solve(G, s, pred=True)
+        assert_exact(g, s, d, p)
+        d64 = oracle.dijkstra_f64(g.row_ptr, g.col, g.w, int(s))
+        df = d.view(np.float32).astype(np.float64)
+        fin = np.isfinite(d64)
+        assert (np.isfinite(df) == fin).all()
+        rel = np.abs(df[fin] - d64[fin]) / np.maximum(d64[fin], 1e-300)
+        assert rel.max() <= 1e-6
+
+
+def test_heavy_vertex_tasks():
+    """A hub of degree 200k is split into arc-range tasks across warps."""
+    n = 200_001
+    edges = [(0, v, (v * 7919) % 1000 + 1) for v in range(1, n)]
+    edges += [(v, v + 1, 3) for v in range(1, n - 1)]
+    g = gg.from_edges(n, edges)
+    G = upload(g)
+    for th in (256, 4096):
+        d, p = gpu_solve(G, 0, pred=True, config=cfg(th_heavy=th, split=512))
+        assert_exact(g, 0, d, p)
+        assert G.stats()["heavy_tasks"] > 0
+
+
+@pytest.mark.parametrize("wt", ["u32", "f32"])
+@pytest.mark.parametrize("pred", [False, True])
+def test_batch_equals_single(wt, pred):
+    g = gg.rmat(13, 16, seed=5, wtype=wt)
+    G = upload(g)
+    srcs, _ = gg.giant_sources(g, 40, seed=2)
+    srcs = np.concatenate([srcs, srcs[:3]])  # repeated sources are independent queries
+    d, p = gpu_batch(G, srcs, pred=pred)
+    for q, s in enumerate(srcs):
+        assert_exact(g, s, d[q], p[q] if pred else None)
+
+
+def test_batch_host_buffers_and_tiny_capacity():
+    g = gg.grid(64, 48, 1, 100, seed=7)
+    G = upload(g, device_inputs=False)
+    srcs = np.array([0, 5, 3071, 100, 2000], np.int32)
+    d, p = gpu_batch(G, srcs, pred=True, host=True, config=cfg(l1_cap=256, bmax=4, bnum=2))
+    for q, s in enumerate(srcs):
+        assert_exact(g, s, d[q], p[q])
+
+
+def test_edge_cases():
+    # a single vertex, no arcs
+    g = gg.from_edges(1, [])
+    G = upload(g)
+    d, p = gpu_solve(G, 0)
+    assert d.tolist() == [0] and p.tolist() == [0]
+    # source without out-arcs
+    g = gg.from_edges(4, [(1, 2, 5), (2, 3, 1)])
+    G = upload(g)
+    d, p = gpu_solve(G, 0)
+    assert d.tolist() == [0, 0xFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF] and p.tolist() == [0, -1, -1, -1]
+    # f32 -0.0 weight reads as +0.0
+    g = gg.from_edges(2, [(0, 1, np.float32(-0.0))], wtype="f32")
+    G = upload(g)
+    d, _ = gpu_solve(G, 0, pred=False)
+    assert d.tolist() == [0, 0]
+
+
+def test_invalid_inputs():
+    lib = S.lib()
+    import ctypes
+    h = ctypes.c_void_p()
+    rp = np.array([0, 1, 2], np.int32)
+    col_bad = np.array([1, 7], np.int32)
+    w = np.array([1, 1], np.uint32)
+    assert lib.sssp_graph_create(rp.ctypes.data, col_bad.ctypes.data, w.ctypes.data, 2, 2, 0,
+                                 ctypes.byref(h)) == S.SSSP_E_BADGRAPH
+    rp_bad = np.array([0, 2, 1], np.int32)
+    col = np.array([1, 0], np.int32)
+    assert lib.sssp_graph_create(rp_bad.ctypes.data, col.ctypes.data, w.ctypes.data, 2, 2, 0,
+                                 ctypes.byref(h)) == S.SSSP_E_BADGRAPH
+    for bad in (np.nan, -1.0, np.inf):
+        wf = np.array([1.0, bad], np.float32)
+        assert lib.sssp_graph_create(rp.ctypes.data, col.ctypes.data, wf.ctypes.data, 2, 2, 1,
+                                     ctypes.byref(h)) == S.SSSP_E_BADGRAPH
+    G = S.Graph(rp, col, w, "u32")
+    d = torch.empty(2, dtype=torch.int32, device="cuda")
+    with pytest.raises(S.SsspError) as ei:
+        G.solve(2, d)
+    assert ei.value.code == S.SSSP_E_INVAL
+    with pytest.raises(S.SsspError) as ei:
+        G.solve(0, d, cfg=cfg(l1_cap=300))
+    assert ei.value.code == S.SSSP_E_INVAL
+
+
+def test_watchdog_timeout_then_recovers():
+    """A 1 ms watchdog on a long solve returns SSSP_E_TIMEOUT; the handle stays usable."""
+    g = gg.grid(1024, 1024, 1, 100, seed=11)
+    G = upload(g)
+    c = cfg(timeout_ms=1, l2_type=S.L2_VECTOR)
+    d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    with pytest.raises(S.SsspError) as ei:
+        G.solve(0, d, None, c)
+    assert ei.value.code == S.SSSP_E_TIMEOUT
+    d2, p2 = gpu_solve(G, 0, pred=True)
+    assert_exact(g, 0, d2, p2)
+
+
+def test_autotune_prior_and_search():
+    g = gg.rmat(13, 16, seed=9)
+    G = upload(g)
+    prior = G.autotune(None, 0)
+    assert prior.delta_u32 >= 1
+    srcs = torch.from_numpy(gg.giant_sources(g, 2, seed=2)[0]).cuda()
+    tuned = G.autotune(srcs, 1500)
+    assert S.sssp_graph_features(G.handle).n == g.n
+    s = int(srcs[0])
+    d, p = gpu_solve(G, s, pred=True)  # cfg=None uses the tuned configuration
+    assert_exact(g, s, d, p)
+    d, p = gpu_solve(G, s, pred=True, config=tuned)
+    assert_exact(g, s, d, p)
