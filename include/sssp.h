@@ -105,7 +105,7 @@ typedef struct sssp_config {
     uint32_t delta_u32;    /* bucket width for u32 graphs (>= 1) */
     float delta_f32;       /* bucket width for f32 graphs (> 0) */
     int32_t bnum;          /* buckets a read scans, from the lowest (1..32) */
-    int32_t bmax;          /* buckets in total, a circular window (1..1024; 1 = L2V) */
+    int32_t bmax;          /* buckets in total, a circular window (1..32; 1 = L2V) */
     float filter_deltas;   /* L1FQ: F = window base + filter_deltas * delta */
     int32_t th_heavy;      /* degree above which a vertex is split into arc-range tasks */
     int32_t split;         /* arcs per task (multiple of 32) */

@@ -51,6 +51,7 @@ enum : int {
     kErrTimeout = 1,      // a bounded wait or the solve watchdog expired
     kErrOverflow = 2,     // every L2 bucket ring was full
     kErrState = 3,        // queue metadata inconsistent at seeding
+    kErrElement = 4,      // a popped element names a vertex or query out of range
 };
 
 // statistics slots (ctrl.stats)
@@ -101,18 +102,20 @@ struct KParams {
     const uint2* adj;        // (col, weight bits) per arc
     int32_t n;
     void* dist;              // uint32_t[nq * n] or unsigned long long[nq * n]
+    int32_t nq;              // number of queries (dist slices)
     int32_t vbits;           // multi-query: key = (query << vbits) | v
     uint32_t vmask;
     Rings l2;
     TaskRing hv;
     Ctrl* ctrl;
     uint32_t delta;          // u32 width, or f32 bits
-    int32_t bnum, bmax;
+    int32_t bnum, bmax;        // bmax <= 32
     int32_t l1_type, l1_cap, wb;
     float filter_deltas;
     int32_t th_heavy, split;
     int32_t l1_off;          // byte offset of the L1 buffer in dynamic shared memory
     unsigned long long timeout_ns;
+    unsigned long long* trace;   // debug only: per-warp (location << 48 | iteration), mapped host memory
 };
 
 // ------------------------------------------------------------------ PTX --
@@ -166,6 +169,11 @@ __device__ __forceinline__ uint2 vld(const volatile uint2* p) {
     unsigned long long x = *(const volatile unsigned long long*)p;
     return make_uint2((uint32_t)x, (uint32_t)(x >> 32));
 }
+
+// Ticket w is ahead of ticket r (wrap-safe): some writer holds ticket r.
+// Any observed w with w - r > 0 proves ticket r was taken, whatever the order
+// in which the two relaxed loads were performed.
+__device__ __forceinline__ bool ahead(uint32_t w, uint32_t r) { return (int32_t)(w - r) > 0; }
 
 // relaxed L2 load of a distance word (bypasses L1 so the filter sees recent values)
 __device__ __forceinline__ uint32_t ld_dist(const uint32_t* p) { return __ldcg(p); }
@@ -290,6 +298,16 @@ struct Worker {
         return ld_volatile_int(&P.ctrl->error) != 0 || ld_volatile_int(&P.ctrl->finished) != 0;
     }
 
+    // debug trace of where this warp is (no-op unless P.trace is set)
+    __device__ __forceinline__ void mark(uint32_t code, uint32_t iter = 0) const {
+        if (P.trace) {
+            const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+            *(volatile unsigned long long*)(P.trace + gt) =
+                ((unsigned long long)code << 48) | (unsigned long long)(iter & 0xffffffffffffull);
+            __threadfence_system();
+        }
+    }
+
     // ---- element helpers
     __device__ __forceinline__ uint32_t key_query(uint32_t key) const { return MQ ? key >> P.vbits : 0u; }
     __device__ __forceinline__ uint32_t key_vertex(uint32_t key) const { return MQ ? key & P.vmask : key; }
@@ -329,9 +347,18 @@ struct Worker {
         __syncwarp();
     }
 
+    // warp-uniform read of a shared-memory word: lane 0 reads, all lanes get
+    // the same value (control flow that depends on it stays convergent)
+    __device__ __forceinline__ uint32_t sread(const uint32_t* p) const {
+        uint32_t v = 0;
+        if (lane == 0) v = *(const volatile uint32_t*)p;
+        return __shfl_sync(kFull, v, 0);
+    }
+
     // ---- L1 lock -----------------------------------------------------------
     __device__ bool lock() {
         int ok = 1;
+        mark(2);
         if (lane == 0) {
             uint32_t spins = 0;
             while (atomicCAS(&S->lock, 0, 1) != 0) {
@@ -343,7 +370,9 @@ struct Worker {
                 __nanosleep(20);
             }
         }
+        mark(42);
         ok = __shfl_sync(kFull, ok, 0);
+        mark(43);
         __threadfence_block();
         return ok != 0;
     }
@@ -393,7 +422,9 @@ struct Worker {
                 for (;;) {
                     uint32_t* wtp = P.l2.wt + (size_t)bucket * 32;
                     uint32_t* rtp = P.l2.rt + (size_t)bucket * 32;
-                    uint32_t w0 = ld_relaxed(wtp), r0 = ld_relaxed(rtp);
+                    // read r before w (acquire) so w - r over-estimates the occupancy
+                    uint32_t r0 = ld_acquire(rtp);
+                    uint32_t w0 = ld_relaxed(wtp);
                     if (w0 - r0 + P.l2.margin < P.l2.nch) {
                         t = atomicAdd(wtp, 1u);
                         break;
@@ -405,6 +436,7 @@ struct Worker {
                     }
                     bucket = (bucket + 1u) % (uint32_t)P.bmax;
                 }
+                mark(3);
                 if (okw) {
                     // wait until the chunk slot of ticket t is free (normally immediate)
                     uint32_t* sp = P.l2.seq + (size_t)bucket * P.l2.nch + (t & (P.l2.nch - 1u));
@@ -441,10 +473,14 @@ struct Worker {
         return total;
     }
 
-    // Reads one chunk from the lowest non-empty bucket of the first bnum
-    // buckets (lane i probes bucket cur + i), or one arc-range task from the
-    // task ring (probed by the last lane; tasks first).  Advances the window
-    // when the first bucket is empty and a later one is not (Section 4.2).
+    // Reads one chunk from the bucket queue, or one arc-range task from the
+    // task ring (probed by lane 31; tasks first).  Lane i probes bucket
+    // cur + i of the circular window (bmax <= 32, so one warp sees every
+    // bucket in one round trip).  Readers take from the non-empty buckets
+    // among the first bnum (Section 4.2, "the first bnum buckets are
+    // checked"), lowest first; when the first bucket is empty the window
+    // moves up to the lowest non-empty bucket ("base is increased by delta
+    // when the first bucket is empty"), even if that is beyond bnum.
     // Returns 0 (nothing), 1 (chunk: elements in lanes) or 2 (task).
     __device__ int global_read(bool& valid, uint2& e, uint4& task) {
         valid = false;
@@ -454,7 +490,7 @@ struct Worker {
         const uint32_t cur = (uint32_t)(win >> 32), base = (uint32_t)win;
         uint32_t b = (cur + lane) % (uint32_t)P.bmax;
         uint32_t r = 0, w = 0;
-        bool probe = lane < (uint32_t)P.bnum;
+        bool probe = lane < (uint32_t)P.bmax;
         if (probe) {
             r = ld_relaxed(P.l2.rt + (size_t)b * 32);
             w = ld_relaxed(P.l2.wt + (size_t)b * 32);
@@ -464,13 +500,15 @@ struct Worker {
             hr = ld_relaxed(P.hv.rt);
             hw = ld_relaxed(P.hv.wt);
         }
-        bool have_task = __shfl_sync(kFull, hr != hw, 31);
+        mark(30);
+        bool have_task = __shfl_sync(kFull, ahead(hw, hr), 31);
+        mark(31);
         if (have_task) {
             int got = 0;
             uint32_t t = 0;
             if (lane == 31) {
                 uint32_t rr = hr;
-                while (rr != hw) {
+                for (int k = 0; k < 8 && ahead(hw, rr); k++) {
                     uint32_t old = atomicCAS(P.hv.rt, rr, rr + 1u);
                     if (old == rr) { got = 1; t = rr; break; }
                     rr = old;
@@ -505,26 +543,31 @@ struct Worker {
                 return 2;
             }
         }
-        uint32_t nonempty = __ballot_sync(kFull, probe && r != w);
+        mark(32);
+        uint32_t nonempty = __ballot_sync(kFull, probe && ahead(w, r));
+        mark(33);
         if (nonempty == 0) return 0;
-        int first = __ffs(nonempty) - 1;
-        // the first bucket of the window is empty: move the window up
-        if (first > 0 && lane == 0) {
-            unsigned long long nw =
-                ((unsigned long long)((cur + (uint32_t)first) % (uint32_t)P.bmax) << 32) |
-                A::advance(base, P.delta, (uint32_t)first);
-            atomicCAS(&P.ctrl->window, win, nw);
+        const int first = __ffs(nonempty) - 1;
+        uint32_t cand = nonempty & (P.bnum >= 32 ? kFull : ((1u << P.bnum) - 1u));
+        if (first > 0) {
+            // the first bucket is empty: move the window to the lowest non-empty one
+            if (lane == 0) {
+                unsigned long long nw =
+                    ((unsigned long long)((cur + (uint32_t)first) % (uint32_t)P.bmax) << 32) |
+                    A::advance(base, P.delta, (uint32_t)first);
+                atomicCAS(&P.ctrl->window, win, nw);
+            }
+            if (cand == 0) cand = 1u << first;
         }
-        // claim a ticket in the lowest non-empty bucket (CAS only while r != w)
+        // claim a ticket in the lowest candidate bucket (CAS only while w is ahead of r)
         int got = 0;
         uint32_t t = 0, cnt = 0, bb = 0;
-        uint32_t cand = nonempty;
         while (cand) {
             int c = __ffs(cand) - 1;
             if (lane == (uint32_t)c) {
                 uint32_t rr = r;
                 uint32_t* rtp = P.l2.rt + (size_t)b * 32;
-                for (int k = 0; k < 8 && rr != w; k++) {
+                for (int k = 0; k < 8 && ahead(w, rr); k++) {
                     uint32_t old = atomicCAS(rtp, rr, rr + 1u);
                     if (old == rr) { got = 1; t = rr; break; }
                     rr = old;
@@ -543,6 +586,7 @@ struct Worker {
         if (!got) return 0;
         const size_t slot = (size_t)bb * P.l2.nch + (t & (P.l2.nch - 1u));
         int okr = 1;
+        mark(4);
         if (lane == 0) {
             uint32_t spins = 0;
             while (ld_acquire(P.l2.seq + slot) != t + 1u) {
@@ -586,14 +630,14 @@ struct Worker {
         if (type == 1) {
             // near-far: two rings of cap/2
             const uint32_t half = cap >> 1;
-            uint32_t nf = *(volatile uint32_t*)&S->nf;
+            uint32_t nf = sread(&S->nf);
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 bool nearv = valid[k] && e[k].y < nf;
                 bool farv = valid[k] && !nearv;
                 uint32_t nm = __ballot_sync(kFull, nearv), fm = __ballot_sync(kFull, farv);
-                uint32_t h = *(volatile uint32_t*)&S->head, t = *(volatile uint32_t*)&S->tail;
-                uint32_t fh = *(volatile uint32_t*)&S->fhead, ft = *(volatile uint32_t*)&S->ftail;
+                uint32_t h = sread(&S->head), t = sread(&S->tail);
+                uint32_t fh = sread(&S->fhead), ft = sread(&S->ftail);
                 uint32_t nspace = half - (t - h), fspace = half - (ft - fh);
                 uint32_t nr = __popc(nm & lanemask_lt()), fr = __popc(fm & lanemask_lt());
                 out[k] = false;
@@ -617,7 +661,7 @@ struct Worker {
             // SLF deque: dist <= head element -> push front, else push back
 #pragma unroll
             for (int k = 0; k < K; k++) {
-                uint32_t h = *(volatile uint32_t*)&S->head, t = *(volatile uint32_t*)&S->tail;
+                uint32_t h = sread(&S->head), t = sread(&S->tail);
                 uint32_t hd = (t != h) ? vld(&L1[h & l1_mask()]).y : 0u;
                 bool front = valid[k] && t != h && e[k].y <= hd;
                 bool back = valid[k] && !front;
@@ -649,7 +693,7 @@ struct Worker {
             for (int k = 0; k < K; k++) {
                 bool want = valid[k] && (type != 2 || e[k].y <= fthr);
                 uint32_t wm = __ballot_sync(kFull, want);
-                uint32_t h = *(volatile uint32_t*)&S->head, t = *(volatile uint32_t*)&S->tail;
+                uint32_t h = sread(&S->head), t = sread(&S->tail);
                 uint32_t space = cap - (t - h);
                 uint32_t rank = __popc(wm & lanemask_lt());
                 out[k] = valid[k] && !want;
@@ -681,7 +725,7 @@ struct Worker {
             for (int ring = 0; ring < 2; ring++) {
                 uint32_t* hp = ring ? &S->fhead : &S->head;
                 uint32_t* tp = ring ? &S->ftail : &S->tail;
-                uint32_t h = *(volatile uint32_t*)hp, t = *(volatile uint32_t*)tp;
+                uint32_t h = sread(hp), t = sread(tp);
                 while (h != t) {
                     uint32_t c = t - h < 32u ? t - h : 32u;
                     bool v = lane < c;
@@ -695,7 +739,7 @@ struct Worker {
                 __syncwarp();
             }
         } else {
-            uint32_t h = *(volatile uint32_t*)&S->head, t = *(volatile uint32_t*)&S->tail;
+            uint32_t h = sread(&S->head), t = sread(&S->tail);
             while (h != t) {
                 uint32_t c = t - h < 32u ? t - h : 32u;
                 bool v = lane < c;
@@ -750,14 +794,16 @@ struct Worker {
             uint32_t fh0 = *(volatile uint32_t*)&S->fhead, ft0 = *(volatile uint32_t*)&S->ftail;
             any = any || fh0 != ft0;
         }
+        mark(40);
         if (!__any_sync(kFull, any)) return false;
+        mark(41);
         if (!lock()) return false;
         const uint32_t cap = (uint32_t)P.l1_cap;
-        uint32_t h = *(volatile uint32_t*)&S->head, t = *(volatile uint32_t*)&S->tail;
+        uint32_t h = sread(&S->head), t = sread(&S->tail);
         if (P.l1_type == 1 && h == t) {
             // near vector drained: NF = min(far) + delta, then re-partition far
             const uint32_t half = cap >> 1;
-            uint32_t fh = *(volatile uint32_t*)&S->fhead, ft = *(volatile uint32_t*)&S->ftail;
+            uint32_t fh = sread(&S->fhead), ft = sread(&S->ftail);
             if (fh != ft) {
                 uint32_t mn = kInfU32;
                 for (uint32_t i = fh + lane; i - fh < ft - fh; i += 32)
@@ -934,6 +980,10 @@ struct Worker {
         uint32_t key = el.x, du = el.y;
         int32_t rs = 0, deg = 0;
         bool stale = false;
+        if (valid && (key_vertex(key) >= (uint32_t)P.n || key_query(key) >= (uint32_t)P.nq)) {
+            raise_error(P.ctrl, kErrElement, 8, (int)key);
+            valid = false;
+        }
         if (valid) {
             uint32_t cur = dpart(ld_dist(dist + dist_index(key)));
             if (du > cur) {
@@ -959,7 +1009,8 @@ struct Worker {
             uint32_t t0 = 0;
             int ok = 0;
             if (lane == 0) {
-                uint32_t w0 = ld_relaxed(P.hv.wt), r0 = ld_relaxed(P.hv.rt);
+                uint32_t r0 = ld_acquire(P.hv.rt);
+                uint32_t w0 = ld_relaxed(P.hv.wt);
                 if (w0 - r0 + ntask + P.hv.margin <= P.hv.nslot) {
                     atomicAdd(&P.ctrl->reserve, (unsigned long long)ntask);
                     t0 = atomicAdd(P.hv.wt, ntask);
@@ -1004,6 +1055,11 @@ struct Worker {
         const uint32_t myq = MQ ? key_query(key) : 0u;
         st[kStRelax] += (uint32_t)total;
         for (int32_t g0 = 0; g0 < total; g0 += 32) {
+            if ((g0 & 4095) == 4064) {
+                int stop = 0;
+                if (lane == 0) stop = expired() || ld_volatile_int(&P.ctrl->error) != 0;
+                if (__shfl_sync(kFull, stop, 0)) break;
+            }
             const int32_t g = g0 + (int32_t)lane;
             // owner: the largest lane j with ex[j] <= g
             int j = 0;
@@ -1042,9 +1098,16 @@ struct Worker {
         uint32_t idle_ns = 0;
         uint32_t iter = 0;
         for (;;) {
+            mark(1, iter);
             if ((++iter & 7u) == 0 || idle_ns) {
                 int stop = 0;
-                if (lane == 0) stop = aborted() || expired();
+                if (lane == 0) {
+                    stop = aborted();
+                    if (!stop && expired()) {
+                        raise_error(P.ctrl, kErrTimeout, 7, 0);
+                        stop = 1;
+                    }
+                }
                 stop = __shfl_sync(kFull, stop, 0);
                 if (stop) break;
             }
@@ -1053,10 +1116,14 @@ struct Worker {
             uint4 task = make_uint4(0, 0, 0, 0);
             int kind = 0;  // 0 none, 1 batch, 2 task
             int nb = 0;
+            mark(20, iter);
             if (l0_read(valid, e)) kind = 1;
+            mark(21, iter);
             if (!kind && l1_read(valid, e)) kind = 1;
+            mark(22, iter);
             if (!kind) kind = global_read(valid, e, task);
             if (kind == 0) {
+                mark(9, iter);
                 // idle: publish deferred decrements, then test termination
                 acct_apply();
                 int fin = 0;
@@ -1075,8 +1142,18 @@ struct Worker {
                 continue;
             }
             idle_ns = 0;
+            mark(kind == 2 ? 8 : 7, iter);
+            if (kind == 2 && (key_vertex(task.x) >= (uint32_t)P.n || key_query(task.x) >= (uint32_t)P.nq ||
+                              (int32_t)task.z < 0 || (int32_t)task.w < (int32_t)task.z)) {
+                raise_error(P.ctrl, kErrElement, 9, (int)task.x);
+                break;
+            }
             if (kind == 2) {
-                uint32_t cur = dpart(ld_dist(dist + dist_index(task.x)));
+                // one lane decides staleness for the whole warp: dist[u] may move
+                // between per-lane loads, and relax_range is warp-collective
+                uint32_t cur = 0;
+                if (lane == 0) cur = dpart(ld_dist(dist + dist_index(task.x)));
+                cur = __shfl_sync(kFull, cur, 0);
                 if (task.y <= cur) relax_range(task.x, task.y, (int32_t)task.z, (int32_t)task.w);
                 else st[kStStale]++;
                 nb = 1;
@@ -1085,8 +1162,10 @@ struct Worker {
                 relax_batch(valid, e);
             }
             dec += nb;
+            mark(10, iter);
             acct_apply();
         }
+        mark(13, iter);
         // drop anything still held (only on abort paths)
         publish_stats();
     }

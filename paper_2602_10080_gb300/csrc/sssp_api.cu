@@ -3,8 +3,11 @@
 // statistics.  Autotuning lives in sssp_autotune.cu, serving in
 // sssp_serve.cu.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <thread>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -386,7 +389,7 @@ static void config_defaults(sssp_config* c) {
     c->delta_u32 = 0;     // 0 = derive from the graph's weights
     c->delta_f32 = 0.0f;
     c->bnum = 4;
-    c->bmax = 64;
+    c->bmax = 32;
     c->filter_deltas = 2.0f;
     c->th_heavy = 2048;
     c->split = 1024;
@@ -422,7 +425,7 @@ int validate_config(const sssp_config* c) {
     if (c->l0_rows != kL0Rows) return SSSP_E_INVAL;
     if (!pow2(c->l1_cap) || c->l1_cap < 256 || c->l1_cap > 16384) return SSSP_E_INVAL;
     if (c->wb < 0) return SSSP_E_INVAL;
-    if (c->bmax < 1 || c->bmax > 1024 || c->bnum < 1 || c->bnum > 32) return SSSP_E_INVAL;
+    if (c->bmax < 1 || c->bmax > 32 || c->bnum < 1 || c->bnum > 32) return SSSP_E_INVAL;
     if (!(c->filter_deltas >= 0.0f)) return SSSP_E_INVAL;
     if (c->th_heavy < 32 || c->split < 32 || (c->split & 31)) return SSSP_E_INVAL;
     if (c->block_threads != 256 && c->block_threads != 512 && c->block_threads != 1024) return SSSP_E_INVAL;
@@ -512,6 +515,7 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
         P.adj = g->adj;
         P.n = n;
         P.dist = work;
+        P.nq = nq;
         P.vbits = mq ? vbits : 0;
         P.vmask = mq ? ((1u << vbits) - 1u) : 0xffffffffu;
         P.l2 = ws.rings;
@@ -538,8 +542,24 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
                 (uint32_t*)work, cells, g->wtype == SSSP_W_F32 ? kInfF32 : kInfU32);
         seed_kernel<<<1, 32, 0, stream>>>(P, srcs_d, src0, nq, pred_mode ? 1 : 0);
         cudaEventRecord(ws.ev1, stream);
+        if (std::getenv("SSSP_DEBUG") && std::atoi(std::getenv("SSSP_DEBUG")) > 2)
+            std::fprintf(stderr, "[sssp] launch wt=%d pred=%d mq=%d nq=%d n=%d grid=%d threads=%d smem=%zu "
+                                 "bmax=%d bnum=%d l1=%d nch=%u\n", key.wt, key.pred, key.mq, nq, n, grid, threads,
+                         smem, P.bmax, P.bnum, P.l1_type, P.l2.nch);
+        const int dbg = std::getenv("SSSP_DEBUG") ? std::atoi(std::getenv("SSSP_DEBUG")) : 0;
+        unsigned long long* trace_h = nullptr;
+        const size_t nwarps_total = (size_t)grid * threads;  // per-thread records
+        if (dbg > 2 && cudaHostAlloc((void**)&trace_h, nwarps_total * 8, cudaHostAllocMapped) == cudaSuccess) {
+            std::memset(trace_h, 0, nwarps_total * 8);
+            cudaHostGetDevicePointer((void**)&P.trace, trace_h, 0);
+        }
         ce = launch_mlmq(key, dim3(grid), dim3(threads), smem, stream, P);
-        if (ce != cudaSuccess) return cuda_status(ce);
+        if (ce != cudaSuccess) {
+            if (std::getenv("SSSP_DEBUG"))
+                std::fprintf(stderr, "[sssp] launch failed: %s (grid=%d threads=%d smem=%zu)\n",
+                             cudaGetErrorString(ce), grid, threads, smem);
+            return cuda_status(ce);
+        }
         cudaEventRecord(ws.ev2, stream);
         // outputs
         if (pred_mode) {
@@ -564,8 +584,42 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
             cudaMemcpyAsync(dist_out, work, cells * 4, cudaMemcpyDeviceToHost, stream);
         }
         cudaMemcpyAsync(ws.host_ctrl, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream);
+        if (trace_h) {
+            // debug: poll instead of blocking; report where warps sit if the solve overruns
+            auto t0 = std::chrono::steady_clock::now();
+            bool reported = false;
+            while (cudaStreamQuery(stream) == cudaErrorNotReady) {
+                double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+                if (!reported && el > (double)tmo + 3000.0) {
+                    unsigned long long hist[64] = {0};
+                    for (size_t i = 0; i < nwarps_total; i++) hist[(trace_h[i] >> 48) & 63]++;
+                    std::fprintf(stderr, "[sssp] OVERRUN %.0f ms; warps by location:", el);
+                    for (int c = 0; c < 64; c++)
+                        if (hist[c]) std::fprintf(stderr, " %d:%llu", c, hist[c]);
+                    std::fprintf(stderr, "\n");
+                    for (size_t wv = 0; wv < nwarps_total / 32; wv++) {
+                        bool live = false;
+                        for (int l = 0; l < 32; l++)
+                            if ((unsigned)(trace_h[wv * 32 + l] >> 48) != 13) live = true;
+                        if (!live) continue;
+                        std::fprintf(stderr, "[sssp]  warp %zu (block %zu):", wv, wv / (threads / 32));
+                        for (int l = 0; l < 32; l++)
+                            std::fprintf(stderr, " %u/%llu", (unsigned)(trace_h[wv * 32 + l] >> 48),
+                                         trace_h[wv * 32 + l] & 0xffffffffffffull);
+                        std::fprintf(stderr, "\n");
+                    }
+                    reported = true;
+                }
+                std::this_thread::sleep_for(std::chrono::milliseconds(1));
+            }
+            cudaFreeHost(trace_h);
+        }
         ce = cudaStreamSynchronize(stream);
-        if (ce != cudaSuccess) return cuda_status(ce);
+        if (ce != cudaSuccess) {
+            if (std::getenv("SSSP_DEBUG"))
+                std::fprintf(stderr, "[sssp] stream error: %s\n", cudaGetErrorString(ce));
+            return cuda_status(ce);
+        }
         const Ctrl& hc = *ws.host_ctrl;
         float ms_kernel = 0, ms_total = 0;
         cudaEventElapsedTime(&ms_kernel, ws.ev1, ws.ev2);
@@ -591,7 +645,19 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
         st.attempts = attempts;
         g->last = st;
         if (st_out) *st_out = st;
+        if (std::getenv("SSSP_DEBUG") && std::atoi(std::getenv("SSSP_DEBUG")) > 1)
+            std::fprintf(stderr, "[sssp] nq=%d n=%d kernel %.3f ms pops l0/l1/l2/heavy %lld/%lld/%lld/%lld relax %lld "
+                                 "improved %lld stale %lld chunks %lld tasks %lld err %d fin %d\n",
+                         nq, n, ms_kernel, (long long)st.pops_l0, (long long)st.pops_l1, (long long)st.pops_l2,
+                         (long long)st.pops_heavy, (long long)st.relax_arcs, (long long)st.improved,
+                         (long long)st.stale, (long long)st.l2_chunks_written, (long long)st.heavy_tasks,
+                         hc.error, hc.finished);
         if (hc.error == kErrNone && hc.finished) return SSSP_OK;
+        if (std::getenv("SSSP_DEBUG"))
+            std::fprintf(stderr, "[sssp] solve failed: error=%d where=%d info=%d finished=%d reserve=%llu done=%llu "
+                                 "window=%llx grid=%d threads=%d smem=%zu\n",
+                         hc.error, hc.err_where, hc.err_info, hc.finished, hc.reserve, hc.done, hc.window, grid,
+                         threads, smem);
         // failure: the queue metadata is no longer consistent
         ws.dirty = true;
         if (hc.error == kErrOverflow && attempts < 4) {

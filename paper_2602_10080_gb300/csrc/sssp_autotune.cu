@@ -41,14 +41,14 @@ sssp_config prior_config(const Graph* g) {
             c.l2_type = SSSP_L2_BUCKET;
             c.filter_deltas = 2.0f;
             c.bnum = 4;
-            c.bmax = 64;
+            c.bmax = 32;
             break;
         case kMesh:
             c.l1_type = SSSP_L1_FILTER;
             c.l2_type = SSSP_L2_BUCKET;
             c.filter_deltas = 4.0f;
             c.bnum = 8;
-            c.bmax = 64;
+            c.bmax = 32;
             break;
         case kRoad:
             if (f.n < 500000) {
@@ -62,7 +62,7 @@ sssp_config prior_config(const Graph* g) {
                 c.l2_type = SSSP_L2_BUCKET;
                 c.bnum = 4;
             }
-            c.bmax = 128;
+            c.bmax = 32;
             break;
     }
     c.delta_u32 = 0;

@@ -69,7 +69,7 @@ def test_random_graphs_stress(seed):
     lo = 0 if seed % 4 == 1 else 1
     g = gg.random_directed(n, m, lo=lo, hi=int(rng.integers(1, 1000)), seed=seed, wtype=wt)
     G = upload(g)
-    c = cfg(l1_type=L1_ALL[seed % 4], l2_type=seed % 2, l1_cap=256, bmax=int(rng.choice([1, 2, 8, 64])),
+    c = cfg(l1_type=L1_ALL[seed % 4], l2_type=seed % 2, l1_cap=256, bmax=int(rng.choice([1, 2, 8, 32])),
             bnum=int(rng.choice([1, 2, 4])), th_heavy=32, split=32, wb=int(rng.choice([0, 1, 4])),
             block_threads=int(rng.choice([256, 512, 1024])))
     if wt == "u32":
