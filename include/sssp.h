@@ -99,20 +99,27 @@ typedef enum { SSSP_L2_VECTOR = 0, SSSP_L2_BUCKET = 1 } sssp_l2_type;
 typedef struct sssp_config {
     int32_t l1_type;       /* sssp_l1_type */
     int32_t l2_type;       /* sssp_l2_type */
-    int32_t l0_rows;       /* L0 capacity per warp in rows of 32 elements: 1, 2 or 4 */
+    int32_t l0_rows;       /* L0 capacity per warp in rows of 32 elements (compiled: 2) */
     int32_t l1_cap;        /* L1 capacity per thread block, elements (256..16384, power of two) */
     int32_t wb;            /* L1V: flush L1 to L2 after every wb write calls (0 = never) */
-    uint32_t delta_u32;    /* bucket width for u32 graphs (>= 1) */
-    float delta_f32;       /* bucket width for f32 graphs (> 0) */
-    int32_t bnum;          /* buckets a read scans, from the lowest (1..32) */
+    uint32_t delta_u32;    /* bucket width for u32 graphs (0 = derived from the weights) */
+    float delta_f32;       /* bucket width for f32 graphs (0 = derived from the weights) */
+    int32_t bnum;          /* buckets a read may take from, counted from the lowest non-empty (1..32) */
     int32_t bmax;          /* buckets in total, a circular window (1..32; 1 = L2V) */
     float filter_deltas;   /* L1FQ: F = window base + filter_deltas * delta */
-    int32_t th_heavy;      /* degree above which a vertex is split into arc-range tasks */
-    int32_t split;         /* arcs per task (multiple of 32) */
+    float near_deltas;     /* light-arc bound in deltas: a write through an arc of weight
+                              <= near_deltas * delta enters L0/L1, a heavier one goes to its L2
+                              bucket (0 = every write enters L0, as in Listing 1) */
+    int32_t max_arcs;      /* arcs one warp relaxes per batch; later vertices wait in L0 (>= 32) */
+    int32_t claim;         /* L2 chunks one L1 refill claims at once (1..8) */
+    int32_t shards;        /* rings per L2 bucket (1, 2, 4, 8, 16 or 32) */
+    int32_t refillers;     /* warps of one block that may refill L1 from L2 at the same time (1..32) */
+    int32_t stage;         /* 1: a block pools heavy-arc writes per L2 bucket in shared memory and
+                              sends full chunks (0: each warp writes its own groups) */
     int32_t block_threads; /* threads per block: 256, 512 or 1024 */
     int32_t blocks_per_sm; /* resident blocks per SM (0 = as many as fit) */
-    int32_t timeout_ms;    /* device watchdog for one solve (0 = library default) */
-    int32_t reserved[7];   /* must be zero */
+    int32_t timeout_ms;    /* device watchdog for one solve (0 = library default, 20 s) */
+    int32_t reserved[3];   /* must be zero */
 } sssp_config;
 
 /* Graph features of Table 2 (Section 3.5), computed at creation. */
@@ -121,8 +128,9 @@ typedef struct sssp_features {
     double avg_deg, max_deg, std_deg;
     double avg_w, max_w, std_w;
     double min_w;
-    int32_t symmetric;            /* 1 if every arc has a reverse arc of equal weight */
+    int32_t symmetric;            /* 1 if every arc has a reverse arc of equal weight, -1 unknown */
     int32_t has_zero_w;
+    int64_t shadows;              /* shadow vertices of the device layout (split hubs) */
 } sssp_features;
 
 /* Counters of the last solve on a graph (Fig. 3 quantities). */
@@ -135,7 +143,12 @@ typedef struct sssp_stats {
     int64_t relax_arcs;           /* arcs scanned (work) */
     int64_t improved;             /* successful relaxations (writes back) */
     int64_t stale;                /* popped elements already superseded */
-    int64_t l2_chunks_written, l1_flushes, heavy_tasks;
+    int64_t l2_chunks_written, l1_flushes, far_pushes;
+    int64_t cas_fail;             /* failed ticket claims on the L2 rings */
+    int64_t refills, deferred;    /* L1 refills from L2; batch vertices deferred to L0 */
+    int64_t relax_shadow;         /* arcs scanned from shadow vertices (split hubs) */
+    int64_t cycles[6];            /* SM cycles summed over warps: relax, L1 read, L2 write,
+                                     L2/task read, idle, L0 read */
     int32_t grid_blocks, block_threads;
     int32_t attempts;             /* > 1 if the queue was regrown after an overflow */
 } sssp_stats;
@@ -151,7 +164,10 @@ SSSP_API int sssp_config_default(sssp_config *cfg);
 /* ------------------------------------------------------------------ graph -- */
 
 /* Copies a CSR graph to the device, validates it and derives the layout the
- * kernels use (interleaved (col, weight) pairs, one 8-byte load per arc).
+ * kernels use: interleaved (col, weight) pairs (one 8-byte load per arc),
+ * and every vertex with more than `split` arcs (1024) represented by
+ * zero-weight shadow vertices that each own a slice of at most `split`
+ * arcs, so the arcs of a hub are relaxed by many warps at once.
  *   row_ptr  int32[n + 1], col_idx int32[m], weights uint32[m] or fp32[m]
  *            (per `wtype`); host or device memory, borrowed (copied).
  *   n >= 1, 0 <= m < 2^31.

@@ -41,9 +41,10 @@ class sssp_config(ctypes.Structure):
         ("l1_type", ctypes.c_int32), ("l2_type", ctypes.c_int32), ("l0_rows", ctypes.c_int32),
         ("l1_cap", ctypes.c_int32), ("wb", ctypes.c_int32), ("delta_u32", ctypes.c_uint32),
         ("delta_f32", ctypes.c_float), ("bnum", ctypes.c_int32), ("bmax", ctypes.c_int32),
-        ("filter_deltas", ctypes.c_float), ("th_heavy", ctypes.c_int32), ("split", ctypes.c_int32),
-        ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-        ("timeout_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+        ("filter_deltas", ctypes.c_float), ("near_deltas", ctypes.c_float), ("max_arcs", ctypes.c_int32),
+        ("claim", ctypes.c_int32), ("shards", ctypes.c_int32), ("refillers", ctypes.c_int32),
+        ("stage", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+        ("timeout_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
     ]
 
     def as_dict(self) -> dict:
@@ -55,7 +56,7 @@ class sssp_features(ctypes.Structure):
         ("n", ctypes.c_int64), ("m", ctypes.c_int64), ("avg_deg", ctypes.c_double),
         ("max_deg", ctypes.c_double), ("std_deg", ctypes.c_double), ("avg_w", ctypes.c_double),
         ("max_w", ctypes.c_double), ("std_w", ctypes.c_double), ("min_w", ctypes.c_double),
-        ("symmetric", ctypes.c_int32), ("has_zero_w", ctypes.c_int32),
+        ("symmetric", ctypes.c_int32), ("has_zero_w", ctypes.c_int32), ("shadows", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -63,18 +64,24 @@ class sssp_features(ctypes.Structure):
 
 
 class sssp_stats(ctypes.Structure):
+    CYCLE_NAMES = ("relax", "l1_read", "l2_write", "global_read", "idle", "l0_read")
+
     _fields_ = [
         ("kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("reached", ctypes.c_int64),
         ("reached_arcs", ctypes.c_int64), ("pops_l0", ctypes.c_int64), ("pops_l1", ctypes.c_int64),
         ("pops_l2", ctypes.c_int64), ("pops_heavy", ctypes.c_int64), ("relax_arcs", ctypes.c_int64),
         ("improved", ctypes.c_int64), ("stale", ctypes.c_int64),
         ("l2_chunks_written", ctypes.c_int64), ("l1_flushes", ctypes.c_int64),
-        ("heavy_tasks", ctypes.c_int64), ("grid_blocks", ctypes.c_int32),
+        ("far_pushes", ctypes.c_int64), ("cas_fail", ctypes.c_int64), ("refills", ctypes.c_int64),
+        ("deferred", ctypes.c_int64), ("relax_shadow", ctypes.c_int64), ("cycles", ctypes.c_int64 * 6),
+        ("grid_blocks", ctypes.c_int32),
         ("block_threads", ctypes.c_int32), ("attempts", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "cycles"}
+        d["cycles"] = dict(zip(self.CYCLE_NAMES, list(self.cycles)))
+        return d
 
 
 _lib = None

@@ -12,12 +12,10 @@ namespace sssp {
 
 // Device buffers reused across solves on one graph.
 struct Workspace {
-    char* ring_mem = nullptr;     // L2 bucket rings (data, tickets, seq, cnt)
-    char* task_mem = nullptr;     // arc-range task ring
+    char* ring_mem = nullptr;     // L2 rings (data, tickets, seq, cnt)
     size_t ring_bytes = 0;
     Rings rings{};
-    TaskRing hv{};
-    uint32_t bmax = 0;
+    uint32_t nrings = 0;          // bmax * shards
     bool dirty = true;            // metadata must be reset before the next solve
     int grow_shift = 0;           // capacity doublings after overflows
     Ctrl* ctrl = nullptr;
@@ -34,19 +32,22 @@ struct Workspace {
     size_t srcs_n = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
 
-    int ensure_queue(uint32_t nbuckets, uint32_t nch, uint32_t margin, uint32_t nslot,
-                     cudaStream_t s, int sms);
+    int ensure_queue(uint32_t nrings, uint32_t nch, uint32_t margin, cudaStream_t s, int sms);
     void release();
 };
 
 struct Graph {
     int device = 0;
     int sms = 1;
-    int32_t n = 0;
-    int64_t m = 0;
+    int32_t n = 0;                // real vertices
+    int64_t m = 0;                // real arcs
+    int32_t nv = 0;               // vertices of the device layout (real + shadow)
+    int64_t mv = 0;               // arcs of the device layout
+    int32_t split = 0;            // arcs per shadow vertex (0 = none split)
     int32_t wtype = 0;
-    int32_t* row_ptr = nullptr;   // [n + 1]
-    uint2* adj = nullptr;         // [m] (col, weight bits)
+    int32_t* row_ptr = nullptr;   // [nv + 1]
+    uint2* adj = nullptr;         // [mv] (col, weight bits)
+    int32_t* owner = nullptr;     // [nv - n]
     sssp_features feat{};
     sssp_config defaults{};
     sssp_config tuned{};

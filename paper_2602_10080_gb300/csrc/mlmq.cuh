@@ -11,20 +11,33 @@
 //   L1  per thread block, in shared memory, behind a warp-granular lock:
 //       Vector / Near-far / Filter / SLF policies (Section 3.4, Fig. 7).
 //   L2  whole grid, in global memory: bmax circular delta-buckets
-//       (Section 4.2, "L2 Bucket queue"), each a ring of 32-element chunks
-//       moved with ONE atomic per chunk (Section 4.2, "L2 FIFO queue",
-//       Listing 3), plus a ring of arc-range tasks for very high degree
-//       vertices (the load balancing of Section 4.1, widened across warps).
+//       (Section 4.2, "L2 Bucket queue"); every bucket is S rings (shards)
+//       of 32-element chunks moved with one ticket per claim (Section 4.2,
+//       "L2 FIFO queue", Listing 3).
 //
 // Spill and refill follow the cache-like collaboration of Section 3.2: the
 // worker touches L0; an empty level refills from the next one down, a full
-// level writes back to it.
+// level writes back to it.  On this GPU the refill of L1 from L2 is done by
+// ONE warp of the block at a time (the others keep working or wait on
+// shared memory), which keeps the number of agents contending for the L2
+// tickets at the number of blocks instead of the number of warps, and a
+// claim takes several chunks at once.  Vertices improved through a heavy arc
+// (weight above near_deltas * delta) skip the local levels and go to their
+// L2 bucket; only light-arc improvements are processed locally at once --
+// the light/heavy arc split of delta-stepping, which keeps local processing
+// from running ahead of the bucket order (the redundant-wavefront concern of
+// Section 2.3).
+//
+// High-degree vertices are split when the graph is created into zero-weight
+// "shadow" vertices that own slices of the arcs, so their arcs are spread
+// over warps and blocks through the same queues (load balancing of
+// Section 4.1 widened beyond one warp).
 //
 // Termination (Section 4.1, delayed counting): every element written to L2
-// (or the task ring) first adds to ctrl.reserve; elements read from L2 are
-// counted in the block's `acct` word, whose high half counts elements the
-// block holds (L0 + L1 + in flight) and whose low half counts L2 reads not
-// yet published.  When the high half reaches zero the low half is added to
+// first adds to ctrl.reserve; elements read from L2 are counted in the
+// block's `acct` word, whose high half counts elements the block holds (L0 +
+// L1 + staging + in flight) and whose low half counts L2 reads not yet
+// published.  When the high half reaches zero the low half is added to
 // ctrl.done.  An idle warp reads done THEN reserve; equality proves that no
 // element is live anywhere.
 //
@@ -41,6 +54,9 @@ namespace sssp {
 constexpr int kWarp = 32;
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kChunk = 32;          // elements per L2 chunk
+constexpr int kFarCap = 64;         // per-warp far staging (elements)
+constexpr int kMaxClaim = 8;        // chunks per L2 claim (upper bound)
+constexpr int kStageCap = 64;       // block staging per L2 bucket (elements)
 constexpr uint32_t kInfU32 = 0xffffffffu;
 constexpr uint32_t kSatU32 = 0xfffffffeu;
 constexpr uint32_t kInfF32 = 0x7f800000u;
@@ -56,27 +72,31 @@ enum : int {
 
 // statistics slots (ctrl.stats)
 enum : int {
-    kStPopL0 = 0, kStPopL1, kStPopL2, kStPopHeavy, kStRelax, kStImproved, kStStale,
-    kStChunks, kStFlush, kStTasks, kStCount
+    kStPopL0 = 0, kStPopL1, kStPopL2, kStRefill, kStRelax, kStImproved, kStStale,
+    kStChunks, kStFlush, kStFar, kStCasFail, kStDeferred, kStRelaxShadow,
+    // SM clock cycles spent per phase (lane 0 of every warp, summed)
+    kCyRelax, kCyL1, kCyL2Write, kCyGlobalRead, kCyIdle, kCyL0,
+    kStCount
 };
 
 struct __align__(128) Ctrl {
-    unsigned long long reserve;          // elements ever written to L2 / tasks
+    unsigned long long reserve;          // elements ever written to L2
     unsigned long long pad0[15];
     unsigned long long done;             // elements read from L2 whose work completed
     unsigned long long pad1[15];
-    unsigned long long window;           // (bucket index << 32) | base distance bits
+    unsigned long long window;           // W: lowest absolute bucket floor(d / delta) that may hold L2 work
     unsigned long long pad2[15];
     int finished;
     int error;
     int err_where;
     int err_info;
     int pad3[28];
-    unsigned long long stats[16];
+    unsigned long long stats[32];
 };
 
-// A set of rings: bucket b uses rt[b * 32], wt[b * 32] (own 128-byte line),
-// seq/cnt[b * nch + s], data[(b * nch + s) * kChunk + i].
+// The L2 rings: ring r = bucket * shards + shard uses rt[r * 32], wt[r * 32]
+// (each on its own 128-byte line), seq/cnt[r * nch + s] and
+// data[(r * nch + s) * kChunk + i].
 struct Rings {
     uint32_t* rt;
     uint32_t* wt;
@@ -87,35 +107,32 @@ struct Rings {
     uint32_t margin;   // free chunks that must remain before a writer may take a ticket
 };
 
-// Arc-range task ring (one task per slot): (key, dist, arc_lo, arc_hi).
-struct TaskRing {
-    uint32_t* rt;
-    uint32_t* wt;
-    uint32_t* seq;
-    uint4* data;
-    uint32_t nslot;    // power of two
-    uint32_t margin;
-};
-
 struct KParams {
-    const int32_t* row_ptr;
+    const int32_t* row_ptr;  // [nv + 1], shadow layout
     const uint2* adj;        // (col, weight bits) per arc
-    int32_t n;
-    void* dist;              // uint32_t[nq * n] or unsigned long long[nq * n]
+    const int32_t* owner;    // [nv - n]: real vertex owning shadow n + i
+    int32_t n;               // real vertices
+    int32_t nv;              // vertices including shadows (stride of a query slice)
     int32_t nq;              // number of queries (dist slices)
+    void* dist;              // uint32_t[nq * nv] or unsigned long long[nq * nv]
     int32_t vbits;           // multi-query: key = (query << vbits) | v
     uint32_t vmask;
     Rings l2;
-    TaskRing hv;
+    int32_t shards;          // rings per bucket (power of two, <= 32)
     Ctrl* ctrl;
     uint32_t delta;          // u32 width, or f32 bits
-    int32_t bnum, bmax;        // bmax <= 32
+    int32_t bnum, bmax;      // bmax <= 32
     int32_t l1_type, l1_cap, wb;
-    float filter_deltas;
-    int32_t th_heavy, split;
-    int32_t l1_off;          // byte offset of the L1 buffer in dynamic shared memory
+    float filter_deltas;     // L1FQ window
+    uint32_t near_w;         // light-arc bound: writes through arcs with weight <= near_w stay
+                             // local (L0/L1), heavier ones go to their L2 bucket (kInfU32 = all local)
+    int32_t max_arcs;        // arcs per warp batch before the rest is deferred
+    int32_t claim;           // chunks per L2 claim (1..kMaxClaim)
+    int32_t refillers;       // warps of a block that may refill L1 from L2 at the same time
+    int32_t stage;           // 1: heavy-arc writes are pooled per bucket in the block before L2
+    int32_t scratch_off, far_off, stat_off, stage_off, l1_off;  // byte offsets in dynamic shared memory
     unsigned long long timeout_ns;
-    unsigned long long* trace;   // debug only: per-warp (location << 48 | iteration), mapped host memory
+    unsigned long long* trace;   // debug only: per-lane (location << 48 | iteration), mapped host memory
 };
 
 // ------------------------------------------------------------------ PTX --
@@ -149,11 +166,6 @@ __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long l
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -175,7 +187,7 @@ __device__ __forceinline__ uint2 vld(const volatile uint2* p) {
 // in which the two relaxed loads were performed.
 __device__ __forceinline__ bool ahead(uint32_t w, uint32_t r) { return (int32_t)(w - r) > 0; }
 
-// relaxed L2 load of a distance word (bypasses L1 so the filter sees recent values)
+// L2 load of a distance word (bypasses L1 so the filter sees recent values)
 __device__ __forceinline__ uint32_t ld_dist(const uint32_t* p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned long long ld_dist(const unsigned long long* p) { return __ldcg(p); }
 
@@ -189,20 +201,12 @@ template <> struct Arith<0> {
         uint32_t s = d + w;
         return (s < d || s == kInfU32) ? kSatU32 : s;
     }
-    // bucket offset of distance d from the window base (0 .. bmax-1)
-    static __device__ __forceinline__ uint32_t offset(uint32_t d, uint32_t base, uint32_t delta,
-                                                      uint32_t last) {
-        if (d <= base) return 0;
-        uint32_t q = (d - base) / delta;
-        return q < last ? q : last;
-    }
-    static __device__ __forceinline__ uint32_t advance(uint32_t base, uint32_t delta, uint32_t k) {
-        unsigned long long b = (unsigned long long)base + (unsigned long long)delta * k;
-        return b > kSatU32 ? kSatU32 : (uint32_t)b;
-    }
-    static __device__ __forceinline__ uint32_t upper(uint32_t base, uint32_t delta, float mult) {
-        unsigned long long b = (unsigned long long)base + (unsigned long long)((double)delta * mult);
-        return b > kSatU32 ? kSatU32 : (uint32_t)b;
+    // absolute bucket of distance d: floor(d / delta)
+    static __device__ __forceinline__ uint32_t bucket(uint32_t d, uint32_t delta) { return d / delta; }
+    // distance bound (W + mult) * delta of the window's first buckets
+    static __device__ __forceinline__ uint32_t upper(uint32_t W, uint32_t delta, float mult) {
+        double b = ((double)W + (double)mult) * (double)delta;
+        return b >= (double)kSatU32 ? kSatU32 : (uint32_t)b;
     }
     static __device__ __forceinline__ uint32_t plus_delta(uint32_t d, uint32_t delta) {
         return add(d, delta);
@@ -216,18 +220,14 @@ template <> struct Arith<1> {
     static __device__ __forceinline__ uint32_t add(uint32_t d, uint32_t w) {
         return __float_as_uint(__fadd_rn(__uint_as_float(d), __uint_as_float(w)));
     }
-    static __device__ __forceinline__ uint32_t offset(uint32_t d, uint32_t base, uint32_t delta,
-                                                      uint32_t last) {
-        float x = (__uint_as_float(d) - __uint_as_float(base)) / __uint_as_float(delta);
-        if (!(x > 0.0f)) return 0;
-        if (x >= (float)last) return last;
+    static __device__ __forceinline__ uint32_t bucket(uint32_t d, uint32_t delta) {
+        float x = __uint_as_float(d) / __uint_as_float(delta);
+        if (!(x > 0.0f)) return 0u;
+        if (x >= 4.0e9f) return 4000000000u;
         return (uint32_t)x;
     }
-    static __device__ __forceinline__ uint32_t advance(uint32_t base, uint32_t delta, uint32_t k) {
-        return __float_as_uint(__uint_as_float(base) + __uint_as_float(delta) * (float)k);
-    }
-    static __device__ __forceinline__ uint32_t upper(uint32_t base, uint32_t delta, float mult) {
-        return __float_as_uint(__uint_as_float(base) + __uint_as_float(delta) * mult);
+    static __device__ __forceinline__ uint32_t upper(uint32_t W, uint32_t delta, float mult) {
+        return __float_as_uint(((float)W + mult) * __uint_as_float(delta));
     }
     static __device__ __forceinline__ uint32_t plus_delta(uint32_t d, uint32_t delta) {
         return __float_as_uint(__uint_as_float(d) + __uint_as_float(delta));
@@ -237,13 +237,14 @@ template <> struct Arith<1> {
 // ------------------------------------------------------ block shared state --
 
 struct BlockShared {
-    int lock;
+    int lock;                     // L1 lock (one warp at a time)
+    int refill;                   // one warp of the block refills L1 from L2
     uint32_t head, tail;          // L1 ring (V, FQ, SLF) or the near ring (NF)
     uint32_t fhead, ftail;        // NF far ring
     uint32_t nf;                  // NF threshold (distance bits)
     uint32_t writes;              // L1 write calls (periodic flush)
-    uint32_t pad;
     unsigned long long acct;      // (held elements << 32) | unpublished L2 reads
+    uint32_t scnt[32];            // elements staged per L2 bucket ring index
 };
 
 // ------------------------------------------------------------- watchdog --
@@ -269,6 +270,8 @@ struct Worker {
     const KParams& P;
     BlockShared* S;
     uint2* scratch;               // this warp's 32-element staging area
+    uint2* farbuf;                // this warp's far staging (kFarCap elements)
+    uint2* stg;                   // block staging, kStageCap elements per L2 bucket ring index
     volatile uint2* L1;           // block L1 buffer
     DistT* dist;
     uint32_t lane;
@@ -277,19 +280,27 @@ struct Worker {
     // L0 ring
     uint2 l0[R];
     uint32_t l0h, l0t;
+    uint32_t nfar;                // elements in farbuf (warp-uniform)
     // deferred accounting (see acct_apply)
-    int unc;                      // L0 pushes not yet counted in S->acct
+    int unc;                      // private pushes (L0, far staging) not yet counted in S->acct
     int dec;                      // completed / exported elements not yet subtracted
-    // statistics (per warp)
-    uint32_t st[kStCount];
+    // statistics (per warp, in shared memory; lane 0 updates)
+    unsigned long long* sst;
 
-    __device__ Worker(const KParams& p, BlockShared* s, uint2* scr, uint2* l1, unsigned long long dl)
-        : P(p), S(s), scratch(scr), L1(l1), dist(reinterpret_cast<DistT*>(p.dist)),
-          lane(lane_id()), deadline(dl), l0h(0), l0t(0), unc(0), dec(0) {
-#pragma unroll
-        for (int i = 0; i < kStCount; i++) st[i] = 0;
+    __device__ Worker(const KParams& p, BlockShared* s, uint2* scr, uint2* far, uint2* stage, uint2* l1,
+                      unsigned long long* stats, unsigned long long dl)
+        : P(p), S(s), scratch(scr), farbuf(far), stg(stage), L1(l1), dist(reinterpret_cast<DistT*>(p.dist)),
+          lane(lane_id()), deadline(dl), l0h(0), l0t(0), nfar(0), unc(0), dec(0),
+          sst(stats) {
+        if (lane == 0)
+            for (int i = 0; i < kStCount; i++) sst[i] = 0;
 #pragma unroll
         for (int r = 0; r < R; r++) l0[r] = make_uint2(0, 0);
+    }
+
+    // warp-uniform statistic update (lane 0 writes)
+    __device__ __forceinline__ void stat(int i, unsigned long long v) const {
+        if (lane == 0) sst[i] += v;
     }
 
     __device__ __forceinline__ bool expired() const { return gtime() > deadline; }
@@ -298,7 +309,7 @@ struct Worker {
         return ld_volatile_int(&P.ctrl->error) != 0 || ld_volatile_int(&P.ctrl->finished) != 0;
     }
 
-    // debug trace of where this warp is (no-op unless P.trace is set)
+    // debug trace of where each lane is (no-op unless P.trace is set)
     __device__ __forceinline__ void mark(uint32_t code, uint32_t iter = 0) const {
         if (P.trace) {
             const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -312,10 +323,18 @@ struct Worker {
     __device__ __forceinline__ uint32_t key_query(uint32_t key) const { return MQ ? key >> P.vbits : 0u; }
     __device__ __forceinline__ uint32_t key_vertex(uint32_t key) const { return MQ ? key & P.vmask : key; }
     __device__ __forceinline__ size_t dist_index(uint32_t key) const {
-        return MQ ? (size_t)key_query(key) * (size_t)P.n + key_vertex(key) : (size_t)key;
+        return MQ ? (size_t)key_query(key) * (size_t)P.nv + key_vertex(key) : (size_t)key;
     }
     static __device__ __forceinline__ uint32_t dpart(uint32_t w) { return w; }
     static __device__ __forceinline__ uint32_t dpart(unsigned long long w) { return (uint32_t)(w >> 32); }
+
+    // warp-uniform read of a shared-memory word: lane 0 reads, all lanes get
+    // the same value (control flow that depends on it stays convergent)
+    __device__ __forceinline__ uint32_t sread(const uint32_t* p) const {
+        uint32_t v = 0;
+        if (lane == 0) v = *(const volatile uint32_t*)p;
+        return __shfl_sync(kFull, v, 0);
+    }
 
     // ---- block accounting -----------------------------------------------
     // Increments (elements becoming visible to other warps) are applied before
@@ -347,14 +366,6 @@ struct Worker {
         __syncwarp();
     }
 
-    // warp-uniform read of a shared-memory word: lane 0 reads, all lanes get
-    // the same value (control flow that depends on it stays convergent)
-    __device__ __forceinline__ uint32_t sread(const uint32_t* p) const {
-        uint32_t v = 0;
-        if (lane == 0) v = *(const volatile uint32_t*)p;
-        return __shfl_sync(kFull, v, 0);
-    }
-
     // ---- L1 lock -----------------------------------------------------------
     __device__ bool lock() {
         int ok = 1;
@@ -370,9 +381,7 @@ struct Worker {
                 __nanosleep(20);
             }
         }
-        mark(42);
         ok = __shfl_sync(kFull, ok, 0);
-        mark(43);
         __threadfence_block();
         return ok != 0;
     }
@@ -383,237 +392,228 @@ struct Worker {
         __syncwarp();
     }
 
-    // ---- L2: bucket rings -------------------------------------------------
+    // ---- L2: sharded bucket rings -----------------------------------------
     __device__ __forceinline__ unsigned long long window() const {
         return ld_acquire64(&P.ctrl->window);
     }
+    __device__ __forceinline__ uint32_t home_shard() const {
+        return (blockIdx.x + (threadIdx.x >> 5)) & (uint32_t)(P.shards - 1);
+    }
 
-    // Writes the valid lanes' elements to the L2 bucket of their distance.
-    // Lanes are grouped per bucket with __match_any_sync; each group fills
-    // one chunk with a single ticket (atomicAdd) on that bucket's ring.
-    // ctrl.reserve grows BEFORE any chunk is published.  Returns the number
-    // of elements written (warp-uniform); the caller defers the decrement.
+    // Writes the valid lanes' elements to the L2 bucket of their distance
+    // (this warp's shard of it).  Lanes are grouped per bucket with
+    // __match_any_sync and every group fills one chunk with a single ticket
+    // (atomicAdd) on its ring; the group leaders take their tickets and
+    // publish concurrently, so a write costs about two round trips whatever
+    // the number of groups.  A shadow vertex (a slice of a hub's arcs) is a
+    // chunk of its own.  ctrl.reserve grows BEFORE any chunk is published.
+    // Returns the number of elements written (warp-uniform); the caller
+    // defers the decrement.
     __device__ int l2_write(bool valid, uint2 e) {
-        uint32_t vm = __ballot_sync(kFull, valid);
+        const uint32_t vm = __ballot_sync(kFull, valid);
         if (vm == 0) return 0;
-        int total = __popc(vm);
+        const long long cw0 = clock64();
+        mark(3);
+        const int total = __popc(vm);
         unsigned long long win = 0;
         if (lane == 0) {
             atomicAdd(&P.ctrl->reserve, (unsigned long long)total);
             win = window();
         }
         win = __shfl_sync(kFull, win, 0);
-        const uint32_t cur = (uint32_t)(win >> 32), base = (uint32_t)win;
-        const uint32_t last = (uint32_t)P.bmax - 1u;
-        uint32_t off = valid ? A::offset(e.y, base, P.delta, last) : 0u;
-        uint32_t b = (cur + off) % (uint32_t)P.bmax;
-        uint32_t pending = vm;
-        while (pending) {
-            int leader = __ffs(pending) - 1;
-            uint32_t bl = __shfl_sync(kFull, b, leader);
-            uint32_t grp = __ballot_sync(kFull, valid && b == bl) & pending;
-            uint32_t t = 0, bucket = bl;
-            int okw = 1;
-            if (lane == (uint32_t)leader) {
-                // take a ticket on the first ring (from bl towards the window end)
-                // that still has `margin` free chunks; diverting an element to a
-                // later bucket only delays it (results are order independent).
-                uint32_t tries = 0;
-                for (;;) {
-                    uint32_t* wtp = P.l2.wt + (size_t)bucket * 32;
-                    uint32_t* rtp = P.l2.rt + (size_t)bucket * 32;
-                    // read r before w (acquire) so w - r over-estimates the occupancy
-                    uint32_t r0 = ld_acquire(rtp);
-                    uint32_t w0 = ld_relaxed(wtp);
-                    if (w0 - r0 + P.l2.margin < P.l2.nch) {
-                        t = atomicAdd(wtp, 1u);
-                        break;
-                    }
-                    if (++tries >= (uint32_t)P.bmax) {
-                        raise_error(P.ctrl, kErrOverflow, 2, (int)bucket);
+        const uint32_t W = (uint32_t)win;
+        const uint32_t shard = home_shard();
+        // absolute bucket; beyond the window span -> the window's last bucket
+        uint32_t ab = valid ? A::bucket(e.y, P.delta) : W;
+        if (ab > W && ab - W >= (uint32_t)P.bmax) ab = W + (uint32_t)P.bmax - 1u;
+        const uint32_t b = ab % (uint32_t)P.bmax;
+        const uint32_t below = __reduce_min_sync(kFull, valid ? ab : 0xffffffffu);
+        const bool shadow = valid && key_vertex(e.x) >= (uint32_t)P.n;
+        const uint32_t gkey = !valid ? 0xffffffffu : (shadow ? (0x80000000u | lane) : b);
+        const uint32_t grp = __match_any_sync(kFull, gkey);
+        const bool leader = valid && (grp & lanemask_lt()) == 0u;
+        uint32_t t = 0, ring = b * (uint32_t)P.shards + shard;
+        int okw = 1;
+        if (leader) {
+            // take a ticket on the first ring (from b towards the window end)
+            // with `margin` free chunks; diverting an element to a later bucket
+            // only delays it (results are order independent).
+            uint32_t tries = 0, bucket = b;
+            for (;;) {
+                uint32_t* wtp = P.l2.wt + (size_t)ring * 32;
+                uint32_t* rtp = P.l2.rt + (size_t)ring * 32;
+                // read r before w (acquire) so w - r over-estimates the occupancy
+                const uint32_t r0 = ld_acquire(rtp);
+                const uint32_t w0 = ld_relaxed(wtp);
+                if (w0 - r0 + P.l2.margin < P.l2.nch) {
+                    t = atomicAdd(wtp, 1u);
+                    break;
+                }
+                if (++tries >= (uint32_t)P.bmax) {
+                    raise_error(P.ctrl, kErrOverflow, 2, (int)bucket);
+                    okw = 0;
+                    break;
+                }
+                bucket = (bucket + 1u) % (uint32_t)P.bmax;
+                ring = bucket * (uint32_t)P.shards + shard;
+            }
+            if (okw) {
+                // wait until the chunk slot of ticket t is free (normally immediate)
+                uint32_t* sp = P.l2.seq + (size_t)ring * P.l2.nch + (t & (P.l2.nch - 1u));
+                uint32_t spins = 0;
+                while (ld_acquire(sp) != t) {
+                    if ((++spins & 255u) == 0 && expired()) {
+                        raise_error(P.ctrl, kErrTimeout, 3, (int)ring);
                         okw = 0;
                         break;
                     }
-                    bucket = (bucket + 1u) % (uint32_t)P.bmax;
-                }
-                mark(3);
-                if (okw) {
-                    // wait until the chunk slot of ticket t is free (normally immediate)
-                    uint32_t* sp = P.l2.seq + (size_t)bucket * P.l2.nch + (t & (P.l2.nch - 1u));
-                    uint32_t spins = 0;
-                    while (ld_acquire(sp) != t) {
-                        if ((++spins & 255u) == 0 && expired()) {
-                            raise_error(P.ctrl, kErrTimeout, 3, (int)bucket);
-                            okw = 0;
-                            break;
-                        }
-                        __nanosleep(32);
-                    }
+                    __nanosleep(32);
                 }
             }
-            okw = __shfl_sync(kFull, okw, leader);
-            if (!okw) return total;
-            t = __shfl_sync(kFull, t, leader);
-            bucket = __shfl_sync(kFull, bucket, leader);
-            const size_t slot = (size_t)bucket * P.l2.nch + (t & (P.l2.nch - 1u));
-            if (grp & (1u << lane)) {
-                int rank = __popc(grp & lanemask_lt());
-                P.l2.data[slot * kChunk + rank] = e;
-            }
-            __syncwarp();
-            if (lane == (uint32_t)leader) {
-                P.l2.cnt[slot] = (uint32_t)__popc(grp);
-                __threadfence();
-                st_release(P.l2.seq + slot, t + 1u);
-            }
-            st[kStChunks]++;
-            pending &= ~grp;
         }
+        const int ldr = __ffs(grp) - 1;
+        t = __shfl_sync(kFull, t, ldr);
+        ring = __shfl_sync(kFull, ring, ldr);
+        okw = __shfl_sync(kFull, okw, ldr);
+        if (!__all_sync(kFull, okw || !valid)) return total;
+        const size_t slot = (size_t)ring * P.l2.nch + (t & (P.l2.nch - 1u));
+        if (valid) P.l2.data[slot * kChunk + __popc(grp & lanemask_lt())] = e;
         __syncwarp();
+        if (leader) {
+            P.l2.cnt[slot] = (uint32_t)__popc(grp);
+            __threadfence();
+            st_release(P.l2.seq + slot, t + 1u);
+        }
+        stat(kStChunks, (unsigned long long)__popc(__ballot_sync(kFull, leader)));
+        __syncwarp();
+        // written below the window (work done out of order produced smaller
+        // distances): pull the window back so readers see these buckets first
+        if (lane == 0 && below < W) atomicMin(&P.ctrl->window, (unsigned long long)below);
+        stat(kCyL2Write, (unsigned long long)(clock64() - cw0));
         return total;
     }
 
-    // Reads one chunk from the bucket queue, or one arc-range task from the
-    // task ring (probed by lane 31; tasks first).  Lane i probes bucket
-    // cur + i of the circular window (bmax <= 32, so one warp sees every
-    // bucket in one round trip).  Readers take from the non-empty buckets
-    // among the first bnum (Section 4.2, "the first bnum buckets are
-    // checked"), lowest first; when the first bucket is empty the window
-    // moves up to the lowest non-empty bucket ("base is increased by delta
-    // when the first bucket is empty"), even if that is beyond bnum.
-    // Returns 0 (nothing), 1 (chunk: elements in lanes) or 2 (task).
-    __device__ int global_read(bool& valid, uint2& e, uint4& task) {
-        valid = false;
+    // Probes the L2 rings of the window, lowest absolute bucket first: lane i
+    // looks at absolute bucket W + round * (32 / S) + i / S, shard
+    // (home + i) % S.  When the lowest buckets are empty the window moves up
+    // to the lowest non-empty one ("base is increased by delta when the first
+    // bucket is empty", Section 4.2); the skipped buckets are probed again
+    // after the move and the window goes back if one of them was written in
+    // the meantime (writers below the window also pull it back), so no work
+    // is left behind it.  Claims up to `want` chunks of the lowest non-empty
+    // ring among the first bnum buckets with one CAS on its read ticket.
+    // Returns the number of chunks claimed (warp-uniform) with their ring and
+    // first ticket.
+    __device__ uint32_t l2_claim(uint32_t want, uint32_t& ring_out, uint32_t& t_out) {
         unsigned long long win = 0;
         if (lane == 0) win = window();
         win = __shfl_sync(kFull, win, 0);
-        const uint32_t cur = (uint32_t)(win >> 32), base = (uint32_t)win;
-        uint32_t b = (cur + lane) % (uint32_t)P.bmax;
-        uint32_t r = 0, w = 0;
-        bool probe = lane < (uint32_t)P.bmax;
-        if (probe) {
-            r = ld_relaxed(P.l2.rt + (size_t)b * 32);
-            w = ld_relaxed(P.l2.wt + (size_t)b * 32);
-        }
-        uint32_t hr = 0, hw = 0;
-        if (lane == 31 && P.hv.nslot) {
-            hr = ld_relaxed(P.hv.rt);
-            hw = ld_relaxed(P.hv.wt);
-        }
-        mark(30);
-        bool have_task = __shfl_sync(kFull, ahead(hw, hr), 31);
-        mark(31);
-        if (have_task) {
-            int got = 0;
-            uint32_t t = 0;
-            if (lane == 31) {
-                uint32_t rr = hr;
-                for (int k = 0; k < 8 && ahead(hw, rr); k++) {
-                    uint32_t old = atomicCAS(P.hv.rt, rr, rr + 1u);
-                    if (old == rr) { got = 1; t = rr; break; }
-                    rr = old;
-                    hw = ld_relaxed(P.hv.wt);
-                }
-                if (got) {
-                    uint32_t* sp = P.hv.seq + (t & (P.hv.nslot - 1u));
-                    uint32_t spins = 0;
-                    while (ld_acquire(sp) != t + 1u) {
-                        if ((++spins & 255u) == 0 && expired()) {
-                            raise_error(P.ctrl, kErrTimeout, 4, 0);
-                            got = 0;
+        const uint32_t W = (uint32_t)win;
+        const uint32_t S_ = (uint32_t)P.shards, per = 32u / S_;
+        const uint32_t home = home_shard();
+        for (uint32_t r0 = 0; r0 < (uint32_t)P.bmax; r0 += per) {
+            const uint32_t rel = r0 + lane / S_;
+            const bool probe = rel < (uint32_t)P.bmax;
+            const uint32_t ring = ((W + rel) % (uint32_t)P.bmax) * S_ + ((home + lane) & (S_ - 1u));
+            uint32_t r = 0, w = 0;
+            if (probe) {
+                r = ld_relaxed(P.l2.rt + (size_t)ring * 32);
+                w = ld_relaxed(P.l2.wt + (size_t)ring * 32);
+            }
+            const bool ne = probe && ahead(w, r);
+            const uint32_t nonempty = __ballot_sync(kFull, ne);
+            if (nonempty == 0) continue;
+            const int first = __ffs(nonempty) - 1;
+            const uint32_t first_rel = r0 + (uint32_t)first / S_;
+            if (first_rel > 0) {
+                int moved = 0;
+                if (lane == 0) moved = atomicCAS(&P.ctrl->window, win, (unsigned long long)(W + first_rel)) == win;
+                moved = __shfl_sync(kFull, moved, 0);
+                if (moved) {
+                    // re-probe the skipped buckets (all shards): a writer may have
+                    // published there between the probe and the move
+                    for (uint32_t q0 = 0; q0 < first_rel * S_; q0 += 32) {
+                        const uint32_t qi = q0 + lane;
+                        const bool pr = qi < first_rel * S_;
+                        const uint32_t qring = ((W + qi / S_) % (uint32_t)P.bmax) * S_ + (qi & (S_ - 1u));
+                        bool back = false;
+                        if (pr) back = ahead(ld_relaxed(P.l2.wt + (size_t)qring * 32),
+                                             ld_relaxed(P.l2.rt + (size_t)qring * 32));
+                        const uint32_t bm = __ballot_sync(kFull, back);
+                        if (bm) {
+                            if (lane == 0)
+                                atomicMin(&P.ctrl->window, (unsigned long long)(W + (q0 + __ffs(bm) - 1) / S_));
                             break;
                         }
-                        __nanosleep(32);
-                    }
-                    if (got) {
-                        task = P.hv.data[t & (P.hv.nslot - 1u)];
-                        atomicAdd(&S->acct, (1ull << 32) | 1ull);
-                        __threadfence();
-                        st_release(sp, t + P.hv.nslot);
                     }
                 }
             }
-            got = __shfl_sync(kFull, got, 31);
-            if (got) {
-                task.x = __shfl_sync(kFull, task.x, 31);
-                task.y = __shfl_sync(kFull, task.y, 31);
-                task.z = __shfl_sync(kFull, task.z, 31);
-                task.w = __shfl_sync(kFull, task.w, 31);
-                st[kStPopHeavy]++;
-                return 2;
-            }
-        }
-        mark(32);
-        uint32_t nonempty = __ballot_sync(kFull, probe && ahead(w, r));
-        mark(33);
-        if (nonempty == 0) return 0;
-        const int first = __ffs(nonempty) - 1;
-        uint32_t cand = nonempty & (P.bnum >= 32 ? kFull : ((1u << P.bnum) - 1u));
-        if (first > 0) {
-            // the first bucket is empty: move the window to the lowest non-empty one
-            if (lane == 0) {
-                unsigned long long nw =
-                    ((unsigned long long)((cur + (uint32_t)first) % (uint32_t)P.bmax) << 32) |
-                    A::advance(base, P.delta, (uint32_t)first);
-                atomicCAS(&P.ctrl->window, win, nw);
-            }
-            if (cand == 0) cand = 1u << first;
-        }
-        // claim a ticket in the lowest candidate bucket (CAS only while w is ahead of r)
-        int got = 0;
-        uint32_t t = 0, cnt = 0, bb = 0;
-        while (cand) {
-            int c = __ffs(cand) - 1;
-            if (lane == (uint32_t)c) {
-                uint32_t rr = r;
-                uint32_t* rtp = P.l2.rt + (size_t)b * 32;
-                for (int k = 0; k < 8 && ahead(w, rr); k++) {
-                    uint32_t old = atomicCAS(rtp, rr, rr + 1u);
-                    if (old == rr) { got = 1; t = rr; break; }
-                    rr = old;
-                    w = ld_relaxed(P.l2.wt + (size_t)b * 32);
+            // candidates: non-empty rings of buckets within bnum of the first one
+            uint32_t cand = __ballot_sync(kFull, ne && rel < first_rel + (uint32_t)P.bnum);
+            while (cand) {
+                int c = __ffs(cand) - 1;
+                uint32_t got = 0, t = 0;
+                if (lane == (uint32_t)c) {
+                    uint32_t rr = r;
+                    uint32_t* rtp = P.l2.rt + (size_t)ring * 32;
+                    for (int k = 0; k < 4 && ahead(w, rr); k++) {
+                        uint32_t avail = w - rr;
+                        uint32_t take = avail < want ? avail : want;
+                        uint32_t old = atomicCAS(rtp, rr, rr + take);
+                        if (old == rr) { got = take; t = rr; break; }
+                        rr = old;
+                        w = ld_relaxed(P.l2.wt + (size_t)ring * 32);
+                    }
+                    if (!got) atomicAdd((unsigned long long*)&sst[kStCasFail], 1ull);
                 }
-                bb = b;
+                got = __shfl_sync(kFull, got, c);
+                if (got) {
+                    t_out = __shfl_sync(kFull, t, c);
+                    ring_out = __shfl_sync(kFull, ring, c);
+                    return got;
+                }
+                cand &= ~(1u << c);
             }
-            got = __shfl_sync(kFull, got, c);
-            if (got) {
-                t = __shfl_sync(kFull, t, c);
-                bb = __shfl_sync(kFull, bb, c);
-                break;
-            }
-            cand &= ~(1u << c);
+            return 0;  // the lowest buckets are contended: back off and retry later
         }
-        if (!got) return 0;
-        const size_t slot = (size_t)bb * P.l2.nch + (t & (P.l2.nch - 1u));
-        int okr = 1;
+        return 0;
+    }
+
+    // Waits for the claimed chunks t .. t + got - 1 of `ring` (lane j watches
+    // chunk j, all in parallel) and returns their element counts in the
+    // lanes (cnt of chunk j in lane j).  okr = false on a timeout.
+    __device__ uint32_t l2_wait_chunks(uint32_t ring, uint32_t t, uint32_t got, bool& okr) {
+        uint32_t cnt = 0;
+        int ok = 1;
         mark(4);
-        if (lane == 0) {
+        if (lane < got) {
+            const size_t slot = (size_t)ring * P.l2.nch + ((t + lane) & (P.l2.nch - 1u));
             uint32_t spins = 0;
-            while (ld_acquire(P.l2.seq + slot) != t + 1u) {
+            while (ld_acquire(P.l2.seq + slot) != t + lane + 1u) {
                 if ((++spins & 255u) == 0 && expired()) {
-                    raise_error(P.ctrl, kErrTimeout, 5, (int)bb);
-                    okr = 0;
+                    raise_error(P.ctrl, kErrTimeout, 5, (int)ring);
+                    ok = 0;
                     break;
                 }
                 __nanosleep(32);
             }
-            if (okr) cnt = P.l2.cnt[slot];
+            if (ok) cnt = P.l2.cnt[slot];
         }
-        okr = __shfl_sync(kFull, okr, 0);
-        if (!okr) return 0;
-        cnt = __shfl_sync(kFull, cnt, 0);
-        valid = lane < cnt;
+        okr = __all_sync(kFull, ok != 0);
+        return cnt;
+    }
+
+    // Reads chunk t + j (count c) into the lanes and frees its slot.
+    __device__ void l2_read_chunk(uint32_t ring, uint32_t tj, uint32_t c, bool& valid, uint2& e) {
+        const size_t slot = (size_t)ring * P.l2.nch + (tj & (P.l2.nch - 1u));
+        valid = lane < c;
         if (valid) e = P.l2.data[slot * kChunk + lane];
         __syncwarp();
         if (lane == 0) {
-            // count the elements as held by this block BEFORE freeing the slot
-            atomicAdd(&S->acct, ((unsigned long long)cnt << 32) | (unsigned long long)cnt);
             __threadfence();
-            st_release(P.l2.seq + slot, t + P.l2.nch);
+            st_release(P.l2.seq + slot, tj + P.l2.nch);
         }
         __syncwarp();
-        st[kStPopL2]++;
-        return 1;
     }
 
     // ---- L1 ------------------------------------------------------------------
@@ -621,10 +621,11 @@ struct Worker {
 
     // Places the valid elements (K per lane) into L1 under the block lock, per
     // the L1 policy; elements that do not fit or are filtered out get their
-    // `out` flag set and must go to L2.  Adds `unc` (uncounted L0 pushes) to
-    // the block count before the lock is released.
+    // `out` flag set and must go to L2.  `count_add` elements are added to the
+    // block count before the lock is released (they become visible here).
     template <int K>
-    __device__ void l1_place(uint2 (&e)[K], bool (&valid)[K], bool (&out)[K], uint32_t fthr) {
+    __device__ void l1_place(uint2 (&e)[K], bool (&valid)[K], bool (&out)[K], uint32_t fthr,
+                             int count_add) {
         const int type = P.l1_type;
         const uint32_t cap = (uint32_t)P.l1_cap;
         if (type == 1) {
@@ -662,7 +663,9 @@ struct Worker {
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 uint32_t h = sread(&S->head), t = sread(&S->tail);
-                uint32_t hd = (t != h) ? vld(&L1[h & l1_mask()]).y : 0u;
+                uint32_t hd = 0;
+                if (lane == 0 && t != h) hd = vld(&L1[h & l1_mask()]).y;
+                hd = __shfl_sync(kFull, hd, 0);
                 bool front = valid[k] && t != h && e[k].y <= hd;
                 bool back = valid[k] && !front;
                 uint32_t fm = __ballot_sync(kFull, front), bm = __ballot_sync(kFull, back);
@@ -709,11 +712,8 @@ struct Worker {
                 __syncwarp();
             }
         }
-        // every element that was in L0 is now visible: count the uncounted ones
-        if (lane == 0 && unc != 0) {
-            atomicAdd(&S->acct, ((unsigned long long)(uint32_t)unc) << 32);
-        }
-        unc = 0;
+        if (lane == 0 && count_add != 0)
+            atomicAdd(&S->acct, ((unsigned long long)(uint32_t)count_add) << 32);
     }
 
     // Moves everything in L1 to L2 (periodic flush of L1V, Section 3.4).
@@ -722,15 +722,15 @@ struct Worker {
         const uint32_t cap = (uint32_t)P.l1_cap;
         if (P.l1_type == 1) {
             const uint32_t half = cap >> 1;
-            for (int ring = 0; ring < 2; ring++) {
-                uint32_t* hp = ring ? &S->fhead : &S->head;
-                uint32_t* tp = ring ? &S->ftail : &S->tail;
+            for (int rg = 0; rg < 2; rg++) {
+                uint32_t* hp = rg ? &S->fhead : &S->head;
+                uint32_t* tp = rg ? &S->ftail : &S->tail;
                 uint32_t h = sread(hp), t = sread(tp);
                 while (h != t) {
                     uint32_t c = t - h < 32u ? t - h : 32u;
                     bool v = lane < c;
                     uint2 x = make_uint2(0, 0);
-                    if (v) x = vld(&L1[(ring ? half : 0u) + ((h + lane) & (half - 1u))]);
+                    if (v) x = vld(&L1[(rg ? half : 0u) + ((h + lane) & (half - 1u))]);
                     h += c;
                     dec += l2_write(v, x);
                 }
@@ -752,22 +752,25 @@ struct Worker {
             if (lane == 0) *(volatile uint32_t*)&S->head = h;
             __syncwarp();
         }
-        st[kStFlush]++;
+        stat(kStFlush, 1);
     }
 
-    // Write primitive of the L1 level for K elements per lane.
+    // Write primitive of the L1 level for K elements per lane; `count_add`
+    // of them are not yet in the block count (see l1_place).  `filter`
+    // applies the L1FQ threshold.
     template <int K>
-    __device__ void l1_write(uint2 (&e)[K], bool (&valid)[K]) {
+    __device__ void l1_write(uint2 (&e)[K], bool (&valid)[K], int count_add, bool filter = true) {
+        const long long c0 = clock64();
         uint32_t fthr = kInfU32;
-        if (P.l1_type == 2) {
+        if (P.l1_type == 2 && filter) {
             unsigned long long win = 0;
             if (lane == 0) win = window();
             win = __shfl_sync(kFull, win, 0);
-            fthr = A::upper((uint32_t)win, P.delta, P.filter_deltas);
+            fthr = A::upper((uint32_t)win, P.delta, P.filter_deltas);  // (W + F) * delta
         }
         bool out[K];
         if (!lock()) return;
-        l1_place<K>(e, valid, out, fthr);
+        l1_place<K>(e, valid, out, fthr, count_add);
         bool flush = false;
         if (P.wb > 0) {
             uint32_t wcount = 0;
@@ -780,6 +783,7 @@ struct Worker {
         }
         if (flush) l1_flush_locked();
         unlock();
+        stat(kCyL1, (unsigned long long)((unsigned long long)(clock64() - c0)));
 #pragma unroll
         for (int k = 0; k < K; k++) dec += l2_write(out[k], e[k]);
     }
@@ -787,16 +791,13 @@ struct Worker {
     // Read primitive of the L1 level: up to 32 elements, one per lane.
     __device__ bool l1_read(bool& valid, uint2& e) {
         valid = false;
-        // cheap unlocked emptiness test first
-        uint32_t h0 = *(volatile uint32_t*)&S->head, t0 = *(volatile uint32_t*)&S->tail;
-        bool any = h0 != t0;
-        if (P.l1_type == 1) {
-            uint32_t fh0 = *(volatile uint32_t*)&S->fhead, ft0 = *(volatile uint32_t*)&S->ftail;
-            any = any || fh0 != ft0;
+        // cheap unlocked emptiness test first (lane 0 decides for the warp)
+        uint32_t any = 0;
+        if (lane == 0) {
+            any = *(volatile uint32_t*)&S->head != *(volatile uint32_t*)&S->tail;
+            if (P.l1_type == 1) any |= *(volatile uint32_t*)&S->fhead != *(volatile uint32_t*)&S->ftail;
         }
-        mark(40);
-        if (!__any_sync(kFull, any)) return false;
-        mark(41);
+        if (!__shfl_sync(kFull, any, 0)) return false;
         if (!lock()) return false;
         const uint32_t cap = (uint32_t)P.l1_cap;
         uint32_t h = sread(&S->head), t = sread(&S->tail);
@@ -845,8 +846,72 @@ struct Worker {
         __syncwarp();
         if (lane == 0) *(volatile uint32_t*)&S->head = h + c;
         unlock();
-        if (c) st[kStPopL1]++;
+        if (c) stat(kStPopL1, 1);
         return c != 0;
+    }
+
+    // Free L1 slots (estimate, no lock).
+    __device__ uint32_t l1_free() const {
+        uint32_t f = 0;
+        if (lane == 0) {
+            uint32_t h = *(volatile uint32_t*)&S->head, t = *(volatile uint32_t*)&S->tail;
+            uint32_t cap = (uint32_t)P.l1_cap >> (P.l1_type == 1 ? 1 : 0);
+            uint32_t used = t - h;
+            f = used < cap ? cap - used : 0u;
+        }
+        return __shfl_sync(kFull, f, 0);
+    }
+
+    // L1 is empty: up to `refillers` warps of the block at a time refill it
+    // from L2 (Section 3.2: an empty level triggers a read of the next level).
+    // The first claimed chunk becomes this warp's batch, the rest go to L1.
+    // Returns 1 with a batch in the lanes, 2 if only L1 received elements, 0
+    // if L2 had nothing, -1 if enough warps of the block are already refilling.
+    __device__ int refill(bool& valid, uint2& e) {
+        valid = false;
+        int role = 0;
+        if (lane == 0) {
+            role = atomicAdd(&S->refill, 1) < P.refillers;
+            if (!role) atomicSub(&S->refill, 1);
+        }
+        role = __shfl_sync(kFull, role, 0);
+        if (!role) return -1;
+        stage_flush(false);
+        uint32_t want = (uint32_t)P.claim;
+        const uint32_t room = l1_free() / kChunk;
+        if (want > room + 1u) want = room + 1u;
+        uint32_t ring = 0, t = 0;
+        const uint32_t got = l2_claim(want, ring, t);
+        int result = 0;
+        if (got) {
+            bool okr = true;
+            const uint32_t cnt = l2_wait_chunks(ring, t, got, okr);
+            if (okr) {
+                // the claimed elements are held by this block from now on: count
+                // them before they can be handed to other warps through L1
+                const uint32_t total = __reduce_add_sync(kFull, cnt);
+                if (lane == 0)
+                    atomicAdd(&S->acct, ((unsigned long long)total << 32) | (unsigned long long)total);
+                const uint32_t c0 = __shfl_sync(kFull, cnt, 0);
+                l2_read_chunk(ring, t, c0, valid, e);
+                for (uint32_t j = 1; j < got; j++) {
+                    const uint32_t cj = __shfl_sync(kFull, cnt, j);
+                    bool v2 = false;
+                    uint2 x[1] = {make_uint2(0, 0)};
+                    l2_read_chunk(ring, t + j, cj, v2, x[0]);
+                    bool vv[1] = {v2};
+                    // chunks taken from L2 for processing bypass the L1 filter
+                    l1_write<1>(x, vv, 0, false);
+                }
+                stat(kStPopL2, (unsigned long long)got);
+                stat(kStRefill, 1);
+                result = c0 ? 1 : (total ? 2 : 0);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) atomicSub(&S->refill, 1);
+        __syncwarp();
+        return result;
     }
 
     // ---- L0 ------------------------------------------------------------------
@@ -877,11 +942,17 @@ struct Worker {
             e[r] = l0[r];
         }
         l0h = l0t = 0;
-        l1_write<R>(e, v);
+        // the elements become visible: count every private push now (the
+        // far-staged ones too -- counting early only delays the block's
+        // done flush, counting late could end the solve too soon)
+        const int add = unc;
+        unc = 0;
+        l1_write<R>(e, v, add);
     }
 
-    // Appends c (<= 32) staged elements scratch[0..c) to L0.
-    __device__ void l0_push(uint32_t c) {
+    // Appends c (<= 32) staged elements scratch[0..c) to L0.  `counted`:
+    // they are already in the block count (a deferred batch element).
+    __device__ void l0_push(uint32_t c, bool counted = false) {
         if (c == 0) return;
         if (l0t - l0h + c > 32u * R) l0_spill();
         uint32_t k = (lane - l0t) & 31u;
@@ -890,7 +961,7 @@ struct Worker {
             l0_set((p >> 5) & (R - 1u), scratch[k]);
         }
         l0t += c;
-        unc += (int)c;
+        if (!counted) unc += (int)c;
         __syncwarp();
     }
 
@@ -903,8 +974,126 @@ struct Worker {
         if (valid) e = l0_get(((l0h + k) >> 5) & (R - 1u));
         l0h += c;
         if (l0h == l0t) l0h = l0t = 0;
-        st[kStPopL0]++;
+        stat(kStPopL0, 1);
         return true;
+    }
+
+    // ---- far staging -------------------------------------------------------
+    // Heavy-arc writes wait in a per-warp buffer.  Without block staging they
+    // go to L2 in groups of up to 32.  With block staging (P.stage) the warps
+    // of a block pool them per L2 bucket in shared memory under the L1 lock,
+    // and only full 32-element chunks go to L2 -- one warp's writes spread
+    // over many buckets, so this is what keeps the chunks full.  Writes for
+    // the window's first two buckets are urgent and go to L2 at once; partial
+    // buckets are flushed when they become urgent or the block runs dry.
+
+    __device__ __forceinline__ uint32_t ring_bucket(uint32_t d, uint32_t W, uint32_t& ab) const {
+        ab = A::bucket(d, P.delta);
+        if (ab > W && ab - W >= (uint32_t)P.bmax) ab = W + (uint32_t)P.bmax - 1u;
+        return ab % (uint32_t)P.bmax;
+    }
+
+    // Takes up to 32 staged elements of bucket ring index b (lock held).
+    __device__ uint32_t stage_take(uint32_t b, bool& v, uint2& x) {
+        const uint32_t c0 = sread(&S->scnt[b]);
+        const uint32_t c = c0 < 32u ? c0 : 32u;
+        v = lane < c;
+        if (v) x = stg[b * kStageCap + (c0 - c) + lane];
+        __syncwarp();
+        if (lane == 0) S->scnt[b] = c0 - c;
+        __syncwarp();
+        return c;
+    }
+
+    // Moves staged elements to L2: all buckets (all = true, the block ran
+    // dry) or only those of the window's first two buckets.
+    __device__ void stage_flush(bool all) {
+        if (!P.stage) return;
+        unsigned long long win = 0;
+        if (lane == 0) win = window();
+        const uint32_t W = (uint32_t)__shfl_sync(kFull, win, 0);
+        for (int guard = 0; guard < 64; guard++) {
+            // unlocked look for a non-empty candidate bucket
+            uint32_t cnt = 0;
+            const uint32_t b = lane;
+            const bool cand = b < (uint32_t)P.bmax &&
+                              (all || b == W % (uint32_t)P.bmax || b == (W + 1u) % (uint32_t)P.bmax);
+            if (cand) cnt = *(volatile uint32_t*)&S->scnt[b];
+            const uint32_t m = __ballot_sync(kFull, cand && cnt > 0u);
+            if (!m) return;
+            const uint32_t bf = (uint32_t)(__ffs(m) - 1);
+            bool v = false;
+            uint2 x = make_uint2(0, 0);
+            if (!lock()) return;
+            stage_take(bf, v, x);
+            unlock();
+            dec += l2_write(v, x);
+        }
+    }
+
+    __device__ void far_flush(uint32_t upto) {
+        if (nfar <= upto) return;
+        unsigned long long win = 0;
+        if (P.stage && lane == 0) win = window();
+        const uint32_t W = (uint32_t)__shfl_sync(kFull, win, 0);
+        while (nfar > upto) {
+            const uint32_t take = nfar - upto < 32u ? nfar - upto : 32u;
+            const bool v = lane < take;
+            uint2 x = make_uint2(0, 0);
+            if (v) x = farbuf[nfar - take + lane];
+            __syncwarp();
+            nfar -= take;
+            if (!P.stage) {
+                dec += l2_write(v, x);
+                continue;
+            }
+            uint32_t ab = 0;
+            const uint32_t b = v ? ring_bucket(x.y, W, ab) : 0u;
+            const bool urgent = v && (ab <= W + 1u || key_vertex(x.x) >= (uint32_t)P.n);
+            dec += l2_write(urgent, x);
+            const bool sv = v && !urgent;
+            if (!__any_sync(kFull, sv)) continue;
+            bool vy = false, over = false;
+            uint2 y = make_uint2(0, 0);
+            if (!lock()) return;
+            // the staged elements become visible to the block: count every
+            // private push now (counting early only delays the done flush)
+            if (lane == 0 && unc != 0) atomicAdd(&S->acct, ((unsigned long long)(uint32_t)unc) << 32);
+            unc = 0;
+            const uint32_t grp = __match_any_sync(kFull, sv ? b : 0xffffffffu);
+            const int ldr = __ffs(grp) - 1;
+            uint32_t base = 0;
+            if (sv && lane == (uint32_t)ldr) base = S->scnt[b];
+            base = __shfl_sync(kFull, base, ldr);
+            const uint32_t rank = __popc(grp & lanemask_lt());
+            over = sv && base + rank >= (uint32_t)kStageCap;
+            if (sv && !over) stg[b * kStageCap + base + rank] = x;
+            const uint32_t placed = min((uint32_t)__popc(grp), (uint32_t)kStageCap - min(base, (uint32_t)kStageCap));
+            const bool full = sv && lane == (uint32_t)ldr && base + placed >= 32u;
+            if (sv && lane == (uint32_t)ldr) S->scnt[b] = base + placed;
+            __syncwarp();
+            const uint32_t fm = __ballot_sync(kFull, full);
+            if (fm) {
+                const uint32_t bf = __shfl_sync(kFull, b, __ffs(fm) - 1);
+                stage_take(bf, vy, y);
+            }
+            unlock();
+            dec += l2_write(vy, y);
+            dec += l2_write(over, x);
+        }
+    }
+
+    __device__ void far_push(bool f, uint2 x) {
+        uint32_t m = __ballot_sync(kFull, f);
+        if (!m) return;
+        uint32_t c = __popc(m);
+        if (nfar + c > (uint32_t)kFarCap) far_flush(0);
+        if (f) farbuf[nfar + __popc(m & lanemask_lt())] = x;
+        __syncwarp();
+        nfar += c;
+        unc += (int)c;
+        stat(kStFar, (unsigned long long)(c));
+        if (nfar >= 32u) far_flush(nfar & 31u);
     }
 
     // ---- relaxation ---------------------------------------------------------
@@ -940,47 +1129,35 @@ struct Worker {
         }
     }
 
-    // stage improved elements of one round and push them to L0
-    __device__ __forceinline__ void push_round(bool imp, uint32_t key, uint32_t nd) {
-        uint32_t m = __ballot_sync(kFull, imp);
-        if (m == 0) return;
-        if (imp) scratch[__popc(m & lanemask_lt())] = make_uint2(key, nd);
-        __syncwarp();
-        st[kStImproved] += __popc(m);
-        l0_push(__popc(m));
-    }
-
-    // Relaxes arcs [lo, hi) of one vertex with the whole warp (task path).
-    __device__ void relax_range(uint32_t key, uint32_t du, int32_t lo, int32_t hi) {
-        const uint32_t u = key_vertex(key);
-        const uint32_t qhi = MQ ? (key_query(key) << P.vbits) : 0u;
-        const size_t qoff = MQ ? (size_t)key_query(key) * (size_t)P.n : 0;
-        for (int32_t e0 = lo; e0 < hi; e0 += 64) {
-            int32_t ea = e0 + (int32_t)lane, eb = ea + 32;
-            bool va = ea < hi, vb = eb < hi;
-            uint2 aa = make_uint2(0, 0), ab = make_uint2(0, 0);
-            if (va) aa = __ldg(P.adj + ea);
-            if (vb) ab = __ldg(P.adj + eb);
-            uint32_t nda = 0, ndb = 0;
-            bool ia = va && relax(qoff + aa.x, u, du, aa.y, nda);
-            bool ib = vb && relax(qoff + ab.x, u, du, ab.y, ndb);
-            st[kStRelax] += __popc(__ballot_sync(kFull, va)) + __popc(__ballot_sync(kFull, vb));
-            push_round(ia, qhi | aa.x, nda);
-            push_round(ib, qhi | ab.x, ndb);
+    // route the improved elements of one round: writes through light arcs
+    // (w <= near_w, the light/heavy split of delta-stepping) go to L0, the
+    // others to the far staging and then their L2 bucket
+    __device__ __forceinline__ void push_round(bool imp, uint32_t key, uint32_t nd, uint32_t w) {
+        // a shadow vertex (a slice of a hub's arcs) always goes to L2 so that
+        // the slices of one hub spread over all blocks
+        const bool nearv = imp && w <= P.near_w && key_vertex(key) < (uint32_t)P.n;
+        const uint32_t m = __ballot_sync(kFull, nearv);
+        if (m) {
+            if (nearv) scratch[__popc(m & lanemask_lt())] = make_uint2(key, nd);
+            __syncwarp();
+            l0_push(__popc(m));
         }
+        far_push(imp && !nearv, make_uint2(key, nd));
+        stat(kStImproved, (unsigned long long)(__popc(__ballot_sync(kFull, imp))));
     }
 
     // Relaxes a batch of up to 32 vertices (one per lane).  Stale elements are
-    // dropped (Listing 2: u.dist > dist[u]); vertices above th_heavy become
-    // arc-range tasks; the remaining arcs are spread evenly over the lanes by
-    // a warp prefix sum over degrees (Section 4.1 hybrid load balancing: a
-    // high-degree vertex is scanned by the whole warp, low-degree vertices'
-    // arcs are packed together).
-    __device__ void relax_batch(bool valid, uint2 el) {
+    // dropped (Listing 2: u.dist > dist[u]); the arcs are spread evenly over
+    // the lanes by a warp prefix sum over degrees (Section 4.1 hybrid load
+    // balancing: a high-degree vertex is scanned by the whole warp, low-degree
+    // vertices' arcs are packed together).  Vertices whose arcs start beyond
+    // max_arcs go back to L0 for the next batch.  Returns the number of
+    // elements consumed.
+    __device__ int relax_batch(bool valid, uint2 el) {
         uint32_t key = el.x, du = el.y;
         int32_t rs = 0, deg = 0;
         bool stale = false;
-        if (valid && (key_vertex(key) >= (uint32_t)P.n || key_query(key) >= (uint32_t)P.nq)) {
+        if (valid && (key_vertex(key) >= (uint32_t)P.nv || key_query(key) >= (uint32_t)P.nq)) {
             raise_error(P.ctrl, kErrElement, 8, (int)key);
             valid = false;
         }
@@ -995,54 +1172,8 @@ struct Worker {
                 deg = __ldg(P.row_ptr + v + 1) - rs;
             }
         }
-        st[kStStale] += __popc(__ballot_sync(kFull, stale));
-        // heavy vertices -> tasks
-        uint32_t hm = __ballot_sync(kFull, valid && deg > P.th_heavy);
-        while (hm) {
-            int hl = __ffs(hm) - 1;
-            hm &= hm - 1u;
-            uint32_t hkey = __shfl_sync(kFull, key, hl);
-            uint32_t hdu = __shfl_sync(kFull, du, hl);
-            int32_t hrs = __shfl_sync(kFull, rs, hl);
-            int32_t hdeg = __shfl_sync(kFull, deg, hl);
-            uint32_t ntask = ((uint32_t)hdeg + (uint32_t)P.split - 1u) / (uint32_t)P.split;
-            uint32_t t0 = 0;
-            int ok = 0;
-            if (lane == 0) {
-                uint32_t r0 = ld_acquire(P.hv.rt);
-                uint32_t w0 = ld_relaxed(P.hv.wt);
-                if (w0 - r0 + ntask + P.hv.margin <= P.hv.nslot) {
-                    atomicAdd(&P.ctrl->reserve, (unsigned long long)ntask);
-                    t0 = atomicAdd(P.hv.wt, ntask);
-                    ok = 1;
-                }
-            }
-            ok = __shfl_sync(kFull, ok, 0);
-            if (!ok) continue;   // ring busy: the warp scans this vertex itself
-            t0 = __shfl_sync(kFull, t0, 0);
-            for (uint32_t i = lane; i < ntask; i += 32) {
-                uint32_t t = t0 + i;
-                uint32_t* sp = P.hv.seq + (t & (P.hv.nslot - 1u));
-                uint32_t spins = 0;
-                bool okw = true;
-                while (ld_acquire(sp) != t) {
-                    if ((++spins & 255u) == 0 && expired()) {
-                        raise_error(P.ctrl, kErrTimeout, 6, 0);
-                        okw = false;
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-                if (!okw) break;
-                int32_t lo = hrs + (int32_t)(i * (uint32_t)P.split);
-                int32_t hi = min(lo + P.split, hrs + hdeg);
-                P.hv.data[t & (P.hv.nslot - 1u)] = make_uint4(hkey, hdu, (uint32_t)lo, (uint32_t)hi);
-                __threadfence();
-                st_release(sp, t + 1u);
-            }
-            st[kStTasks] += ntask;
-            if ((uint32_t)hl == lane) deg = 0;
-        }
+        int consumed = __popc(__ballot_sync(kFull, valid || stale));
+        stat(kStStale, (unsigned long long)(__popc(__ballot_sync(kFull, stale))));
         // exclusive prefix sum of degrees
         int32_t incl = deg;
 #pragma unroll
@@ -1050,10 +1181,42 @@ struct Worker {
             int32_t x = __shfl_up_sync(kFull, incl, o);
             if (lane >= (uint32_t)o) incl += x;
         }
+        int32_t ex = incl - deg;
+        // defer vertices starting beyond max_arcs (never the first one)
+        const bool defer = valid && ex >= P.max_arcs;
+        const uint32_t dm = __ballot_sync(kFull, defer);
+        if (dm) {
+            if (defer) scratch[__popc(dm & lanemask_lt())] = el;
+            __syncwarp();
+            l0_push(__popc(dm), true);
+            consumed -= __popc(dm);
+            stat(kStDeferred, (unsigned long long)(__popc(dm)));
+            if (defer) {
+                valid = false;
+                deg = 0;
+            }
+            incl = deg;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t x = __shfl_up_sync(kFull, incl, o);
+                if (lane >= (uint32_t)o) incl += x;
+            }
+            ex = incl - deg;
+        }
         const int32_t total = __shfl_sync(kFull, incl, 31);
-        const int32_t ex = incl - deg;
         const uint32_t myq = MQ ? key_query(key) : 0u;
-        st[kStRelax] += (uint32_t)total;
+        // predecessor id: a shadow vertex stands for its owner
+        uint32_t pu = 0;
+        if (PRED != 0 && valid) {
+            uint32_t v = key_vertex(key);
+            pu = v < (uint32_t)P.n ? v : (uint32_t)__ldg(P.owner + (v - (uint32_t)P.n));
+        }
+        stat(kStRelax, (unsigned long long)((uint32_t)total));
+        {
+            const int32_t sh = valid && key_vertex(key) >= (uint32_t)P.n ? deg : 0;
+            const int32_t shs = __reduce_add_sync(kFull, (uint32_t)sh);
+            if (shs) stat(kStRelaxShadow, (unsigned long long)shs);
+        }
         for (int32_t g0 = 0; g0 < total; g0 += 32) {
             if ((g0 & 4095) == 4064) {
                 int stop = 0;
@@ -1071,25 +1234,26 @@ struct Worker {
             const int32_t oex = __shfl_sync(kFull, ex, j);
             const int32_t ors = __shfl_sync(kFull, rs, j);
             const uint32_t odu = __shfl_sync(kFull, du, j);
-            const uint32_t okey = __shfl_sync(kFull, key, j);
             const uint32_t oq = __shfl_sync(kFull, myq, j);
+            const uint32_t opu = PRED != 0 ? __shfl_sync(kFull, pu, j) : 0u;
             bool imp = false;
-            uint32_t nd = 0, v = 0;
+            uint32_t nd = 0, v = 0, w = 0;
             if (g < total) {
                 uint2 a = __ldg(P.adj + (ors + (g - oex)));
                 v = a.x;
-                size_t vidx = MQ ? (size_t)oq * (size_t)P.n + v : (size_t)v;
-                imp = relax(vidx, key_vertex(okey), odu, a.y, nd);
+                w = a.y;
+                size_t vidx = MQ ? (size_t)oq * (size_t)P.nv + v : (size_t)v;
+                imp = relax(vidx, opu, odu, w, nd);
             }
-            push_round(imp, MQ ? ((oq << P.vbits) | v) : v, nd);
+            push_round(imp, MQ ? ((oq << P.vbits) | v) : v, nd, w);
         }
+        return consumed;
     }
 
     __device__ void publish_stats() {
         if (lane == 0) {
-#pragma unroll
             for (int i = 0; i < kStCount; i++)
-                if (st[i]) atomicAdd(&P.ctrl->stats[i], (unsigned long long)st[i]);
+                if (sst[i]) atomicAdd(&P.ctrl->stats[i], sst[i]);
         }
     }
 
@@ -1113,21 +1277,36 @@ struct Worker {
             }
             bool valid = false;
             uint2 e = make_uint2(0, 0);
-            uint4 task = make_uint4(0, 0, 0, 0);
-            int kind = 0;  // 0 none, 1 batch, 2 task
-            int nb = 0;
-            mark(20, iter);
-            if (l0_read(valid, e)) kind = 1;
-            mark(21, iter);
-            if (!kind && l1_read(valid, e)) kind = 1;
-            mark(22, iter);
-            if (!kind) kind = global_read(valid, e, task);
-            if (kind == 0) {
+            bool got = false;
+            const long long c0 = clock64();
+            got = l0_read(valid, e);
+            const long long c1 = clock64();
+            stat(kCyL0, (unsigned long long)((unsigned long long)(c1 - c0)));
+            if (!got) got = l1_read(valid, e);
+            const long long c2 = clock64();
+            int rf = 1;
+            if (!got) {
+                // local levels are empty: hand the far staging to L2 first
+                if (nfar) {
+                    far_flush(0);
+                    acct_apply();
+                }
+                rf = refill(valid, e);
+                got = rf == 1;
+            }
+            const long long c3 = clock64();
+            stat(kCyGlobalRead, (unsigned long long)((unsigned long long)(c3 - c2)));
+            if (!got) {
+                if (rf == 2) continue;  // L1 received elements
+                if (rf == 0) {
+                    // nothing in L2 for this block: publish everything it staged
+                    stage_flush(true);
+                    acct_apply();
+                }
                 mark(9, iter);
-                // idle: publish deferred decrements, then test termination
-                acct_apply();
                 int fin = 0;
-                if (lane == 0) {
+                if (rf == 0 && lane == 0) {
+                    // L2 looked empty to this block's refiller: test termination
                     unsigned long long d = ld_acquire64(&P.ctrl->done);
                     unsigned long long r = ld_acquire64(&P.ctrl->reserve);
                     if (d == r) {
@@ -1137,36 +1316,19 @@ struct Worker {
                 }
                 fin = __shfl_sync(kFull, fin, 0);
                 if (fin) break;
-                idle_ns = idle_ns ? min(idle_ns * 2u, 2048u) : 64u;
+                idle_ns = idle_ns ? min(idle_ns * 2u, 1024u) : 64u;
                 __nanosleep(idle_ns);
+                stat(kCyIdle, (unsigned long long)((unsigned long long)(clock64() - c3)));
                 continue;
             }
             idle_ns = 0;
-            mark(kind == 2 ? 8 : 7, iter);
-            if (kind == 2 && (key_vertex(task.x) >= (uint32_t)P.n || key_query(task.x) >= (uint32_t)P.nq ||
-                              (int32_t)task.z < 0 || (int32_t)task.w < (int32_t)task.z)) {
-                raise_error(P.ctrl, kErrElement, 9, (int)task.x);
-                break;
-            }
-            if (kind == 2) {
-                // one lane decides staleness for the whole warp: dist[u] may move
-                // between per-lane loads, and relax_range is warp-collective
-                uint32_t cur = 0;
-                if (lane == 0) cur = dpart(ld_dist(dist + dist_index(task.x)));
-                cur = __shfl_sync(kFull, cur, 0);
-                if (task.y <= cur) relax_range(task.x, task.y, (int32_t)task.z, (int32_t)task.w);
-                else st[kStStale]++;
-                nb = 1;
-            } else {
-                nb = __popc(__ballot_sync(kFull, valid));
-                relax_batch(valid, e);
-            }
-            dec += nb;
+            mark(7, iter);
+            dec += relax_batch(valid, e);
+            stat(kCyRelax, (unsigned long long)((unsigned long long)(clock64() - c3)));
             mark(10, iter);
             acct_apply();
         }
         mark(13, iter);
-        // drop anything still held (only on abort paths)
         publish_stats();
     }
 };
@@ -1175,30 +1337,27 @@ template <int WT, int PRED, bool MQ, int R>
 __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     BlockShared* S = reinterpret_cast<BlockShared*>(smem);
-    const int nw = blockDim.x >> 5;
-    uint2* scratch_all = reinterpret_cast<uint2*>(smem + sizeof(BlockShared));
+    uint2* scratch_all = reinterpret_cast<uint2*>(smem + P.scratch_off);
+    uint2* far_all = reinterpret_cast<uint2*>(smem + P.far_off);
     uint2* l1 = reinterpret_cast<uint2*>(smem + P.l1_off);
+    unsigned long long* stats_all = reinterpret_cast<unsigned long long*>(smem + P.stat_off);
+    uint2* stage = reinterpret_cast<uint2*>(smem + P.stage_off);
     if (threadIdx.x == 0) {
         S->lock = 0;
+        S->refill = 0;
         S->head = S->tail = S->fhead = S->ftail = 0;
-        S->nf = 0;
         S->writes = 0;
         S->acct = 0ull;
+        for (int i = 0; i < 32; i++) S->scnt[i] = 0;
         unsigned long long win = ld_acquire64(&P.ctrl->window);
-        S->nf = Arith<WT>::plus_delta((uint32_t)win, P.delta);
+        S->nf = Arith<WT>::upper((uint32_t)win, P.delta, 1.0f);
     }
     __syncthreads();
     const unsigned long long deadline = gtime() + P.timeout_ns;
     const int warp = threadIdx.x >> 5;
-    (void)nw;
-    Worker<WT, PRED, MQ, R> w(P, S, scratch_all + warp * 32, l1, deadline);
+    Worker<WT, PRED, MQ, R> w(P, S, scratch_all + warp * 32, far_all + warp * kFarCap, stage, l1,
+                              stats_all + warp * kStCount, deadline);
     w.run();
 }
-
-// ------------------------------------------------------------- seeding --
-
-// Fills `count` 32-bit words with `value` (dist initialisation).
-__global__ void fill_u32_kernel(uint32_t* p, size_t count, uint32_t value);
-__global__ void fill_u64_kernel(unsigned long long* p, size_t count, unsigned long long value);
 
 }  // namespace sssp

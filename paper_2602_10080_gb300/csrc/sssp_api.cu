@@ -1,16 +1,16 @@
-// sssp_api.cu -- the C ABI of libsssp.so (include/sssp.h): graph upload and
-// validation, per-graph device workspace, single-source and batched solves,
-// statistics.  Autotuning lives in sssp_autotune.cu, serving in
-// sssp_serve.cu.
+// sssp_api.cu -- the C ABI of libsssp.so (include/sssp.h): graph upload,
+// validation and device layout, per-graph workspace, single-source and
+// batched solves, statistics.  Autotuning lives in sssp_autotune.cu, serving
+// in sssp_serve.cu.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
-#include <thread>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/sssp.h"
@@ -35,9 +35,14 @@ extern "C" const char* sssp_strerror(int status) {
     }
 }
 
-extern "C" int sssp_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+extern "C" int sssp_version(void) { return 2 * 10000 + 0 * 100 + 0; }
 
 namespace sssp {
+
+static int debug_level() {
+    const char* e = std::getenv("SSSP_DEBUG");
+    return e ? std::atoi(e) : 0;
+}
 
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SSSP_OK;
@@ -66,6 +71,12 @@ static uint32_t next_pow2(uint64_t v) {
     return (uint32_t)p;
 }
 
+static int grid_for(size_t count, int sms) {
+    size_t b = (count + 255) / 256;
+    size_t cap = (size_t)sms * 8;
+    return (int)std::max<size_t>(1, std::min(b, cap));
+}
+
 // ------------------------------------------------------------ small kernels
 
 __global__ void fill_u32_kernel(uint32_t* p, size_t count, uint32_t value) {
@@ -80,23 +91,18 @@ __global__ void fill_u64_kernel(unsigned long long* p, size_t count, unsigned lo
     for (; i < count; i += stride) p[i] = value;
 }
 
-// Queue metadata to the empty state: seq[b][s] = s ("free for ticket s").
-__global__ void ring_reset_kernel(Rings r, uint32_t nbuckets, TaskRing hv, Ctrl* ctrl) {
-    size_t total = (size_t)nbuckets * r.nch;
+// Queue metadata to the empty state: seq[r][s] = s ("free for ticket s").
+__global__ void ring_reset_kernel(Rings r, uint32_t nrings, Ctrl* ctrl) {
+    size_t total = (size_t)nrings * r.nch;
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t k = i; k < total; k += stride) {
         r.seq[k] = (uint32_t)(k & (r.nch - 1u));
         r.cnt[k] = 0;
     }
-    for (size_t k = i; k < hv.nslot; k += stride) hv.seq[k] = (uint32_t)k;
-    for (size_t k = i; k < (size_t)nbuckets * 32; k += stride) {
+    for (size_t k = i; k < (size_t)nrings * 32; k += stride) {
         r.rt[k] = 0;
         r.wt[k] = 0;
-    }
-    if (i < 32) {
-        hv.rt[i] = 0;
-        hv.wt[i] = 0;
     }
     if (i == 0) {
         ctrl->reserve = 0;
@@ -121,14 +127,13 @@ __global__ void seed_kernel(KParams P, const int32_t* srcs, int32_t src0, int32_
         C->error = 0;
         C->err_where = 0;
         C->err_info = 0;
-        for (int i = 0; i < 16; i++) C->stats[i] = 0;
-        uint32_t cur = (uint32_t)(C->window >> 32) % (uint32_t)P.bmax;
-        C->window = (unsigned long long)cur << 32;  // base distance 0
-        cur_s = cur;
+        for (int i = 0; i < 32; i++) C->stats[i] = 0;
+        C->window = 0;  // sources sit in absolute bucket 0
+        cur_s = 0;
     }
     __syncwarp();
-    const uint32_t cur = cur_s;
-    uint32_t* wtp = P.l2.wt + (size_t)cur * 32;
+    const uint32_t ring = cur_s * (uint32_t)P.shards;  // bucket 0, shard 0
+    uint32_t* wtp = P.l2.wt + (size_t)ring * 32;
     for (int32_t base = 0; base < nq; base += 32) {
         int32_t q = base + (int32_t)lane;
         bool valid = q < nq;
@@ -137,7 +142,7 @@ __global__ void seed_kernel(KParams P, const int32_t* srcs, int32_t src0, int32_
         if (lane == 0) {
             t = *wtp;
             *wtp = t + 1u;
-            if (P.l2.seq[(size_t)cur * P.l2.nch + (t & (P.l2.nch - 1u))] != t) ok = 0;
+            if (P.l2.seq[(size_t)ring * P.l2.nch + (t & (P.l2.nch - 1u))] != t) ok = 0;
         }
         ok = __shfl_sync(kFull, ok, 0);
         if (!ok) {
@@ -145,12 +150,12 @@ __global__ void seed_kernel(KParams P, const int32_t* srcs, int32_t src0, int32_
             return;
         }
         t = __shfl_sync(kFull, t, 0);
-        const size_t slot = (size_t)cur * P.l2.nch + (t & (P.l2.nch - 1u));
+        const size_t slot = (size_t)ring * P.l2.nch + (t & (P.l2.nch - 1u));
         if (valid) {
             int32_t s = srcs ? srcs[q] : src0;
             uint32_t key = P.vbits ? (((uint32_t)q << P.vbits) | (uint32_t)s) : (uint32_t)s;
             P.l2.data[slot * kChunk + lane] = make_uint2(key, 0u);
-            size_t di = (size_t)q * (size_t)P.n + (size_t)s;
+            size_t di = (size_t)q * (size_t)P.nv + (size_t)s;
             if (packed)
                 reinterpret_cast<unsigned long long*>(P.dist)[di] = (unsigned long long)(uint32_t)s;
             else
@@ -168,17 +173,25 @@ __global__ void seed_kernel(KParams P, const int32_t* srcs, int32_t src0, int32_
     __threadfence();
 }
 
-// (dist << 32 | pred) words -> separate dist / pred arrays.
-__global__ void unpack_kernel(const unsigned long long* w, size_t count, uint32_t* dist,
-                              int32_t* pred, int f32) {
+// Work slices [nq][nv] -> outputs [nq][n]: (dist << 32 | pred) words split
+// into dist / pred (packed), or plain distance words copied (!packed).
+__global__ void unpack_kernel(const void* work, int packed, int32_t nq, int32_t n, int32_t nv,
+                              uint32_t* dist, int32_t* pred, int f32) {
+    const size_t count = (size_t)nq * (size_t)n;
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     size_t stride = (size_t)gridDim.x * blockDim.x;
     for (; i < count; i += stride) {
-        unsigned long long x = w[i];
-        uint32_t d = (uint32_t)(x >> 32);
-        if (f32 && d == kInfU32) d = kInfF32;
-        dist[i] = d;
-        if (pred) pred[i] = (int32_t)(uint32_t)x;
+        size_t q = i / (size_t)n, v = i - q * (size_t)n;
+        size_t src = q * (size_t)nv + v;
+        if (packed) {
+            unsigned long long x = reinterpret_cast<const unsigned long long*>(work)[src];
+            uint32_t d = (uint32_t)(x >> 32);
+            if (f32 && d == kInfU32) d = kInfF32;
+            dist[i] = d;
+            if (pred) pred[i] = (int32_t)(uint32_t)x;
+        } else {
+            dist[i] = reinterpret_cast<const uint32_t*>(work)[src];
+        }
     }
 }
 
@@ -208,6 +221,33 @@ __global__ void pack_kernel(const int32_t* col, const uint32_t* w, int64_t m, in
             if ((wb & 0x80000000u) || (wb & 0x7f800000u) == 0x7f800000u) atomicOr(flags, 4);
         }
         adj[i] = make_uint2((uint32_t)c, wb);
+    }
+}
+
+// Shadow layout: vertex v with sfirst[v] >= 0 gets arcs to its shadows
+// sfirst[v] .. sfirst[v] + k - 1 (weight 0), and shadow j owns the arc slice
+// [j * split, (j + 1) * split) of v.  One warp per vertex.
+__global__ void relayout_kernel(const int32_t* rp0, const uint2* adj0, int32_t n, const int32_t* rp1,
+                                const int32_t* sfirst, int32_t split, uint2* adj1) {
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    for (int64_t v = wid; v < n; v += nw) {
+        const int32_t b0 = rp0[v], e0 = rp0[v + 1];
+        const int32_t s0 = sfirst[v];
+        if (s0 < 0) {
+            const int32_t b1 = rp1[v];
+            for (int32_t e = b0 + (int32_t)lane; e < e0; e += 32) adj1[b1 + (e - b0)] = adj0[e];
+        } else {
+            const int32_t k = (e0 - b0 + split - 1) / split;
+            const int32_t b1 = rp1[v];
+            for (int32_t j = (int32_t)lane; j < k; j += 32) adj1[b1 + j] = make_uint2((uint32_t)(s0 + j), 0u);
+            for (int32_t j = 0; j < k; j++) {
+                const int32_t lo = b0 + j * split, hi = min(e0, lo + split);
+                const int32_t d1 = rp1[s0 + j];
+                for (int32_t e = lo + (int32_t)lane; e < hi; e += 32) adj1[d1 + (e - lo)] = adj0[e];
+            }
+        }
     }
 }
 
@@ -263,17 +303,10 @@ __global__ void features_kernel(const int32_t* row_ptr, int32_t n, const uint2* 
     }
 }
 
-static int grid_for(size_t count, int sms) {
-    size_t b = (count + 255) / 256;
-    size_t cap = (size_t)sms * 8;
-    return (int)std::max<size_t>(1, std::min(b, cap));
-}
-
 // ================================================================ workspace
 
 void Workspace::release() {
     cudaFree(ring_mem);
-    cudaFree(task_mem);
     cudaFree(ctrl);
     cudaFree(d64);
     cudaFree(d32);
@@ -303,8 +336,7 @@ static int grow(T** p, size_t* have, size_t want) {
     return SSSP_OK;
 }
 
-int Workspace::ensure_queue(uint32_t nbuckets, uint32_t nch_want, uint32_t margin,
-                            uint32_t nslot_want, cudaStream_t s, int sms) {
+int Workspace::ensure_queue(uint32_t nr, uint32_t nch_want, uint32_t margin, cudaStream_t s, int sms) {
     if (!ev0) {
         if (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess ||
             cudaEventCreate(&ev2) != cudaSuccess)
@@ -317,28 +349,19 @@ int Workspace::ensure_queue(uint32_t nbuckets, uint32_t nch_want, uint32_t margi
         if (cudaMalloc((void**)&ctrl, sizeof(Ctrl)) != cudaSuccess) return SSSP_E_NOMEM;
         cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s);
     }
-    bool realloc = !ring_mem || nbuckets != bmax || nch_want > rings.nch || nslot_want > hv.nslot;
+    const bool realloc = !ring_mem || nr != nrings || nch_want > rings.nch;
     if (realloc) {
+        const uint32_t nch = std::max(nch_want, nr == nrings ? rings.nch : 0u);
         cudaFree(ring_mem);
-        cudaFree(task_mem);
         ring_mem = nullptr;
-        task_mem = nullptr;
-        uint32_t nch = std::max(nch_want, rings.nch && nbuckets == bmax ? rings.nch : 0u);
-        uint32_t nslot = std::max(nslot_want, hv.nslot);
-        size_t tickets = (size_t)nbuckets * 32 * sizeof(uint32_t);
-        size_t meta = (size_t)nbuckets * nch * sizeof(uint32_t);
-        size_t data = (size_t)nbuckets * nch * kChunk * sizeof(uint2);
-        size_t bytes = 2 * tickets + 2 * meta + data + 256;
+        const size_t tickets = (size_t)nr * 32 * sizeof(uint32_t);
+        const size_t meta = (size_t)nr * nch * sizeof(uint32_t);
+        const size_t data = (size_t)nr * nch * kChunk * sizeof(uint2);
+        const size_t bytes = 2 * tickets + 2 * meta + data + 256;
         if (cudaMalloc((void**)&ring_mem, bytes) != cudaSuccess) {
             cudaGetLastError();
             ring_mem = nullptr;
-            return SSSP_E_NOMEM;
-        }
-        size_t tbytes = 2 * 32 * sizeof(uint32_t) + (size_t)nslot * (sizeof(uint32_t) + sizeof(uint4)) + 256;
-        if (cudaMalloc((void**)&task_mem, tbytes) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(ring_mem);
-            ring_mem = nullptr;
+            nrings = 0;
             return SSSP_E_NOMEM;
         }
         char* p = ring_mem;
@@ -352,24 +375,13 @@ int Workspace::ensure_queue(uint32_t nbuckets, uint32_t nch_want, uint32_t margi
         p += meta;
         rings.cnt = reinterpret_cast<uint32_t*>(p);
         rings.nch = nch;
-        char* q = task_mem;
-        hv.data = reinterpret_cast<uint4*>(q);
-        q += (size_t)nslot * sizeof(uint4);
-        hv.rt = reinterpret_cast<uint32_t*>(q);
-        q += 32 * sizeof(uint32_t);
-        hv.wt = reinterpret_cast<uint32_t*>(q);
-        q += 32 * sizeof(uint32_t);
-        hv.seq = reinterpret_cast<uint32_t*>(q);
-        hv.nslot = nslot;
-        bmax = nbuckets;
-        ring_bytes = bytes + tbytes;
+        nrings = nr;
+        ring_bytes = bytes;
         dirty = true;
     }
     rings.margin = margin;
-    hv.margin = margin;
     if (dirty) {
-        size_t total = std::max<size_t>((size_t)bmax * rings.nch, hv.nslot);
-        ring_reset_kernel<<<grid_for(total, sms), 256, 0, s>>>(rings, bmax, hv, ctrl);
+        ring_reset_kernel<<<grid_for((size_t)nrings * rings.nch, sms), 256, 0, s>>>(rings, nrings, ctrl);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
         dirty = false;
@@ -384,15 +396,19 @@ static void config_defaults(sssp_config* c) {
     c->l1_type = SSSP_L1_FILTER;
     c->l2_type = SSSP_L2_BUCKET;
     c->l0_rows = kL0Rows;
-    c->l1_cap = 4096;
+    c->l1_cap = 2048;
     c->wb = 0;
     c->delta_u32 = 0;     // 0 = derive from the graph's weights
     c->delta_f32 = 0.0f;
-    c->bnum = 4;
+    c->bnum = 2;
     c->bmax = 32;
-    c->filter_deltas = 2.0f;
-    c->th_heavy = 2048;
-    c->split = 1024;
+    c->filter_deltas = 1.0f;
+    c->near_deltas = 1.0f;
+    c->max_arcs = 4096;
+    c->claim = 4;
+    c->refillers = 8;
+    c->stage = 1;
+    c->shards = 8;
     c->block_threads = 512;
     c->blocks_per_sm = 0;
     c->timeout_ms = 0;
@@ -403,13 +419,13 @@ void resolve_auto(const Graph* g, sssp_config* c) {
     const sssp_features& f = g->feat;
     double avgdeg = std::max(1.0, f.avg_deg);
     if (g->wtype == SSSP_W_U32 && c->delta_u32 == 0) {
-        // delta-stepping width: about one average weight scaled by 8/degree,
-        // at least 1 (Meyer & Sanders use ~ w_max / degree).
-        double d = std::max(1.0, f.avg_w * 8.0 / avgdeg);
+        // delta-stepping width: about the average weight over the average
+        // degree (Meyer & Sanders use ~ w_max / degree), at least 1
+        double d = std::max(1.0, f.avg_w * 4.0 / avgdeg);
         c->delta_u32 = (uint32_t)std::min(d, 4.0e9);
     }
     if (g->wtype == SSSP_W_F32 && !(c->delta_f32 > 0.0f)) {
-        double d = std::max(1e-6, f.avg_w * 8.0 / avgdeg);
+        double d = std::max(1e-6, f.avg_w * 4.0 / avgdeg);
         c->delta_f32 = (float)d;
     }
     if (c->l2_type == SSSP_L2_VECTOR) {
@@ -426,11 +442,15 @@ int validate_config(const sssp_config* c) {
     if (!pow2(c->l1_cap) || c->l1_cap < 256 || c->l1_cap > 16384) return SSSP_E_INVAL;
     if (c->wb < 0) return SSSP_E_INVAL;
     if (c->bmax < 1 || c->bmax > 32 || c->bnum < 1 || c->bnum > 32) return SSSP_E_INVAL;
-    if (!(c->filter_deltas >= 0.0f)) return SSSP_E_INVAL;
-    if (c->th_heavy < 32 || c->split < 32 || (c->split & 31)) return SSSP_E_INVAL;
+    if (!(c->filter_deltas >= 0.0f) || !(c->near_deltas >= 0.0f)) return SSSP_E_INVAL;
+    if (c->max_arcs < 32) return SSSP_E_INVAL;
+    if (c->claim < 1 || c->claim > kMaxClaim) return SSSP_E_INVAL;
+    if (c->refillers < 1 || c->refillers > 32) return SSSP_E_INVAL;
+    if (!pow2(c->shards) || c->shards > 32) return SSSP_E_INVAL;
     if (c->block_threads != 256 && c->block_threads != 512 && c->block_threads != 1024) return SSSP_E_INVAL;
     if (c->blocks_per_sm < 0 || c->blocks_per_sm > 8 || c->timeout_ms < 0) return SSSP_E_INVAL;
-    for (int i = 0; i < 7; i++)
+    if (c->stage < 0 || c->stage > 1) return SSSP_E_INVAL;
+    for (int i = 0; i < 3; i++)
         if (c->reserved[i] != 0) return SSSP_E_INVAL;
     return SSSP_OK;
 }
@@ -445,53 +465,59 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
     int rc = validate_config(&cfg);
     if (rc) return rc;
     if (cudaSetDevice(g->device) != cudaSuccess) return SSSP_E_CUDA;
-    const int32_t n = g->n;
+    const int32_t n = g->n, nv = g->nv;
     const bool mq = nq > 1;
     int vbits = 0;
     if (mq) {
-        while (vbits < 31 && (1ll << vbits) < (long long)n) vbits++;
+        while (vbits < 31 && (1ll << vbits) < (long long)nv) vbits++;
         if (vbits == 0) vbits = 1;
         if ((unsigned long long)nq << vbits > (1ull << 32)) return SSSP_E_INVAL;
     }
     const int pred_mode = pred_out ? ((g->wtype == SSSP_W_U32 && g->feat.min_w >= 1.0) ? 1 : 2) : 0;
     const KernelKey key{g->wtype == SSSP_W_F32 ? 1 : 0, pred_mode, mq ? 1 : 0};
+    const int shards = cfg.shards;
 
-    // launch shape
+    // launch shape and shared-memory layout
     const int threads = cfg.block_threads;
     const int warps_per_block = threads / 32;
-    const size_t scratch = (size_t)warps_per_block * 32 * sizeof(uint2);
-    const size_t l1_off = (sizeof(BlockShared) + scratch + 15) & ~size_t(15);
+    const size_t scratch_off = (sizeof(BlockShared) + 15) & ~size_t(15);
+    const size_t far_off = scratch_off + (size_t)warps_per_block * 32 * sizeof(uint2);
+    const size_t stat_off = far_off + (size_t)warps_per_block * kFarCap * sizeof(uint2);
+    const size_t stage_off = stat_off + (size_t)warps_per_block * kStCount * sizeof(unsigned long long);
+    const size_t l1_off = stage_off + (cfg.stage ? (size_t)cfg.bmax * kStageCap * sizeof(uint2) : 0);
     const size_t smem = l1_off + (size_t)cfg.l1_cap * sizeof(uint2);
     int occ = 0;
     cudaError_t ce = occupancy_mlmq(key, threads, smem, &occ);
     if (ce != cudaSuccess) return cuda_status(ce);
     if (occ < 1) return SSSP_E_INVAL;
-    int bps = cfg.blocks_per_sm > 0 ? std::min(cfg.blocks_per_sm, occ) : occ;
+    const int bps = cfg.blocks_per_sm > 0 ? std::min(cfg.blocks_per_sm, occ) : occ;
     const int grid = g->sms * bps;
     const uint32_t warps = (uint32_t)(grid * warps_per_block);
 
     Workspace& ws = g->ws;
-    const size_t cells = (size_t)nq * (size_t)n;
-    // L2 capacity: ~ cells / 8 chunks in total over the buckets, at least
-    // 4x the writer margin per bucket; doubled after an overflow.
+    const size_t cells = (size_t)nq * (size_t)nv;       // work slices
+    const size_t ocells = (size_t)nq * (size_t)n;       // outputs
+    const bool dist_dev = is_device_ptr(dist_out);
+    const bool pred_dev = pred_out && is_device_ptr(pred_out);
+    const int dbg = debug_level();
     int attempts = 0;
     for (;;) {
         attempts++;
-        uint64_t total_chunks = std::max<uint64_t>(cells / 8 + 1024, 1024) << ws.grow_shift;
-        uint32_t nch = next_pow2(std::max<uint64_t>(total_chunks / (uint64_t)cfg.bmax + warps,
-                                                    4ull * warps + (uint64_t)(nq / 32 + 2)));
-        uint32_t nslot = next_pow2(std::max<uint64_t>(65536, 16ull * warps));
-        rc = ws.ensure_queue((uint32_t)cfg.bmax, nch, warps, nslot, stream, g->sms);
+        // L2 capacity: ~ cells / 8 chunks over all rings, at least 2x the
+        // writer margin per ring; doubled after an overflow.
+        const uint32_t nr = (uint32_t)(cfg.bmax * shards);
+        const uint64_t total_chunks = (std::max<uint64_t>(cells / 8, 4096)) << ws.grow_shift;
+        const uint32_t nch = next_pow2(std::max<uint64_t>(total_chunks / nr + warps,
+                                                          2ull * warps + (uint64_t)(nq / 32 + 2)));
+        rc = ws.ensure_queue(nr, nch, warps, stream, g->sms);
         if (rc) return rc;
         // distance work buffer
-        const bool dist_dev = is_device_ptr(dist_out);
-        const bool pred_dev = pred_out && is_device_ptr(pred_out);
         void* work = nullptr;
         if (pred_mode) {
             rc = grow(&ws.d64, &ws.d64_n, cells);
             if (rc) return rc;
             work = ws.d64;
-        } else if (dist_dev) {
+        } else if (dist_dev && nv == n) {
             work = dist_out;
         } else {
             rc = grow(&ws.d32, &ws.d32_n, cells);
@@ -513,13 +539,15 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
         std::memset(&P, 0, sizeof(P));
         P.row_ptr = g->row_ptr;
         P.adj = g->adj;
+        P.owner = g->owner;
         P.n = n;
-        P.dist = work;
+        P.nv = nv;
         P.nq = nq;
+        P.dist = work;
         P.vbits = mq ? vbits : 0;
         P.vmask = mq ? ((1u << vbits) - 1u) : 0xffffffffu;
         P.l2 = ws.rings;
-        P.hv = ws.hv;
+        P.shards = shards;
         P.ctrl = ws.ctrl;
         P.delta = g->wtype == SSSP_W_F32 ? __float_as_uint_host(cfg.delta_f32) : cfg.delta_u32;
         P.bnum = std::min(cfg.bnum, cfg.bmax);
@@ -528,10 +556,24 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
         P.l1_cap = cfg.l1_cap;
         P.wb = cfg.l1_type == SSSP_L1_VECTOR ? cfg.wb : 0;
         P.filter_deltas = cfg.filter_deltas;
-        P.th_heavy = cfg.th_heavy;
-        P.split = cfg.split;
+        if (cfg.near_deltas > 0.0f) {
+            if (g->wtype == SSSP_W_F32)
+                P.near_w = __float_as_uint_host(cfg.delta_f32 * cfg.near_deltas);
+            else
+                P.near_w = (uint32_t)std::min(4294967295.0, (double)cfg.delta_u32 * cfg.near_deltas);
+        } else {
+            P.near_w = kInfU32;   // every write enters L0, as in Listing 1
+        }
+        P.max_arcs = cfg.max_arcs;
+        P.claim = cfg.claim;
+        P.refillers = cfg.refillers;
+        P.scratch_off = (int32_t)scratch_off;
+        P.far_off = (int32_t)far_off;
+        P.stat_off = (int32_t)stat_off;
+        P.stage_off = (int32_t)stage_off;
+        P.stage = cfg.stage ? 1 : 0;
         P.l1_off = (int32_t)l1_off;
-        int tmo = cfg.timeout_ms > 0 ? cfg.timeout_ms : 20000;
+        const int tmo = cfg.timeout_ms > 0 ? cfg.timeout_ms : 20000;
         P.timeout_ns = (unsigned long long)tmo * 1000000ull;
 
         cudaEventRecord(ws.ev0, stream);
@@ -542,62 +584,60 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
                 (uint32_t*)work, cells, g->wtype == SSSP_W_F32 ? kInfF32 : kInfU32);
         seed_kernel<<<1, 32, 0, stream>>>(P, srcs_d, src0, nq, pred_mode ? 1 : 0);
         cudaEventRecord(ws.ev1, stream);
-        if (std::getenv("SSSP_DEBUG") && std::atoi(std::getenv("SSSP_DEBUG")) > 2)
-            std::fprintf(stderr, "[sssp] launch wt=%d pred=%d mq=%d nq=%d n=%d grid=%d threads=%d smem=%zu "
-                                 "bmax=%d bnum=%d l1=%d nch=%u\n", key.wt, key.pred, key.mq, nq, n, grid, threads,
-                         smem, P.bmax, P.bnum, P.l1_type, P.l2.nch);
-        const int dbg = std::getenv("SSSP_DEBUG") ? std::atoi(std::getenv("SSSP_DEBUG")) : 0;
         unsigned long long* trace_h = nullptr;
-        const size_t nwarps_total = (size_t)grid * threads;  // per-thread records
-        if (dbg > 2 && cudaHostAlloc((void**)&trace_h, nwarps_total * 8, cudaHostAllocMapped) == cudaSuccess) {
-            std::memset(trace_h, 0, nwarps_total * 8);
+        const size_t nthreads_total = (size_t)grid * threads;
+        if (dbg > 2 && cudaHostAlloc((void**)&trace_h, nthreads_total * 8, cudaHostAllocMapped) == cudaSuccess) {
+            std::memset(trace_h, 0, nthreads_total * 8);
             cudaHostGetDevicePointer((void**)&P.trace, trace_h, 0);
         }
+        if (dbg > 2)
+            std::fprintf(stderr, "[sssp] launch wt=%d pred=%d mq=%d nq=%d n=%d nv=%d grid=%d threads=%d smem=%zu "
+                                 "bmax=%d shards=%d l1=%d nch=%u\n", key.wt, key.pred, key.mq, nq, n, nv, grid,
+                         threads, smem, P.bmax, P.shards, P.l1_type, P.l2.nch);
         ce = launch_mlmq(key, dim3(grid), dim3(threads), smem, stream, P);
         if (ce != cudaSuccess) {
-            if (std::getenv("SSSP_DEBUG"))
-                std::fprintf(stderr, "[sssp] launch failed: %s (grid=%d threads=%d smem=%zu)\n",
-                             cudaGetErrorString(ce), grid, threads, smem);
+            if (dbg) std::fprintf(stderr, "[sssp] launch failed: %s (grid=%d threads=%d smem=%zu)\n",
+                                  cudaGetErrorString(ce), grid, threads, smem);
+            if (trace_h) cudaFreeHost(trace_h);
             return cuda_status(ce);
         }
         cudaEventRecord(ws.ev2, stream);
         // outputs
-        if (pred_mode) {
+        const bool copy_needed = pred_mode || work != dist_out;
+        if (copy_needed) {
             uint32_t* dd = (uint32_t*)dist_out;
             int32_t* pp = pred_out;
             if (!dist_dev) {
-                rc = grow(&ws.out_d, &ws.out_d_n, cells);
+                rc = grow(&ws.out_d, &ws.out_d_n, ocells);
                 if (rc) return rc;
                 dd = ws.out_d;
             }
-            if (!pred_dev) {
-                rc = grow(&ws.out_p, &ws.out_p_n, cells);
+            if (pred_out && !pred_dev) {
+                rc = grow(&ws.out_p, &ws.out_p_n, ocells);
                 if (rc) return rc;
                 pp = ws.out_p;
             }
-            unpack_kernel<<<grid_for(cells, g->sms), 256, 0, stream>>>(ws.d64, cells, dd, pp,
-                                                                       g->wtype == SSSP_W_F32);
-            if (!dist_dev)
-                cudaMemcpyAsync(dist_out, dd, cells * 4, cudaMemcpyDeviceToHost, stream);
-            if (!pred_dev) cudaMemcpyAsync(pred_out, pp, cells * 4, cudaMemcpyDeviceToHost, stream);
-        } else if (!dist_dev) {
-            cudaMemcpyAsync(dist_out, work, cells * 4, cudaMemcpyDeviceToHost, stream);
+            unpack_kernel<<<grid_for(ocells, g->sms), 256, 0, stream>>>(work, pred_mode ? 1 : 0, nq, n, nv, dd,
+                                                                        pred_mode ? pp : nullptr,
+                                                                        g->wtype == SSSP_W_F32);
+            if (!dist_dev) cudaMemcpyAsync(dist_out, dd, ocells * 4, cudaMemcpyDeviceToHost, stream);
+            if (pred_out && !pred_dev) cudaMemcpyAsync(pred_out, pp, ocells * 4, cudaMemcpyDeviceToHost, stream);
         }
         cudaMemcpyAsync(ws.host_ctrl, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream);
         if (trace_h) {
-            // debug: poll instead of blocking; report where warps sit if the solve overruns
+            // debug: poll instead of blocking; report where lanes sit if the solve overruns
             auto t0 = std::chrono::steady_clock::now();
             bool reported = false;
             while (cudaStreamQuery(stream) == cudaErrorNotReady) {
                 double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
                 if (!reported && el > (double)tmo + 3000.0) {
                     unsigned long long hist[64] = {0};
-                    for (size_t i = 0; i < nwarps_total; i++) hist[(trace_h[i] >> 48) & 63]++;
-                    std::fprintf(stderr, "[sssp] OVERRUN %.0f ms; warps by location:", el);
+                    for (size_t i = 0; i < nthreads_total; i++) hist[(trace_h[i] >> 48) & 63]++;
+                    std::fprintf(stderr, "[sssp] OVERRUN %.0f ms; lanes by location:", el);
                     for (int c = 0; c < 64; c++)
                         if (hist[c]) std::fprintf(stderr, " %d:%llu", c, hist[c]);
                     std::fprintf(stderr, "\n");
-                    for (size_t wv = 0; wv < nwarps_total / 32; wv++) {
+                    for (size_t wv = 0; wv < nthreads_total / 32; wv++) {
                         bool live = false;
                         for (int l = 0; l < 32; l++)
                             if ((unsigned)(trace_h[wv * 32 + l] >> 48) != 13) live = true;
@@ -616,8 +656,7 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
         }
         ce = cudaStreamSynchronize(stream);
         if (ce != cudaSuccess) {
-            if (std::getenv("SSSP_DEBUG"))
-                std::fprintf(stderr, "[sssp] stream error: %s\n", cudaGetErrorString(ce));
+            if (dbg) std::fprintf(stderr, "[sssp] stream error: %s\n", cudaGetErrorString(ce));
             return cuda_status(ce);
         }
         const Ctrl& hc = *ws.host_ctrl;
@@ -633,27 +672,31 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
         st.pops_l0 = (int64_t)hc.stats[kStPopL0];
         st.pops_l1 = (int64_t)hc.stats[kStPopL1];
         st.pops_l2 = (int64_t)hc.stats[kStPopL2];
-        st.pops_heavy = (int64_t)hc.stats[kStPopHeavy];
+        st.refills = (int64_t)hc.stats[kStRefill];
         st.relax_arcs = (int64_t)hc.stats[kStRelax];
         st.improved = (int64_t)hc.stats[kStImproved];
         st.stale = (int64_t)hc.stats[kStStale];
         st.l2_chunks_written = (int64_t)hc.stats[kStChunks];
         st.l1_flushes = (int64_t)hc.stats[kStFlush];
-        st.heavy_tasks = (int64_t)hc.stats[kStTasks];
+        st.far_pushes = (int64_t)hc.stats[kStFar];
+        st.cas_fail = (int64_t)hc.stats[kStCasFail];
+        st.deferred = (int64_t)hc.stats[kStDeferred];
+        st.relax_shadow = (int64_t)hc.stats[kStRelaxShadow];
+        for (int k = 0; k < 6; k++) st.cycles[k] = (int64_t)hc.stats[kCyRelax + k];
         st.grid_blocks = grid;
         st.block_threads = threads;
         st.attempts = attempts;
         g->last = st;
         if (st_out) *st_out = st;
-        if (std::getenv("SSSP_DEBUG") && std::atoi(std::getenv("SSSP_DEBUG")) > 1)
-            std::fprintf(stderr, "[sssp] nq=%d n=%d kernel %.3f ms pops l0/l1/l2/heavy %lld/%lld/%lld/%lld relax %lld "
-                                 "improved %lld stale %lld chunks %lld tasks %lld err %d fin %d\n",
+        if (dbg > 1)
+            std::fprintf(stderr, "[sssp] nq=%d n=%d kernel %.3f ms pops l0/l1/l2 %lld/%lld/%lld refills %lld relax %lld "
+                                 "improved %lld far %lld stale %lld chunks %lld casfail %lld err %d fin %d\n",
                          nq, n, ms_kernel, (long long)st.pops_l0, (long long)st.pops_l1, (long long)st.pops_l2,
-                         (long long)st.pops_heavy, (long long)st.relax_arcs, (long long)st.improved,
-                         (long long)st.stale, (long long)st.l2_chunks_written, (long long)st.heavy_tasks,
-                         hc.error, hc.finished);
+                         (long long)st.refills, (long long)st.relax_arcs, (long long)st.improved,
+                         (long long)st.far_pushes, (long long)st.stale, (long long)st.l2_chunks_written,
+                         (long long)st.cas_fail, hc.error, hc.finished);
         if (hc.error == kErrNone && hc.finished) return SSSP_OK;
-        if (std::getenv("SSSP_DEBUG"))
+        if (dbg)
             std::fprintf(stderr, "[sssp] solve failed: error=%d where=%d info=%d finished=%d reserve=%llu done=%llu "
                                  "window=%llx grid=%d threads=%d smem=%zu\n",
                          hc.error, hc.err_where, hc.err_info, hc.finished, hc.reserve, hc.done, hc.window, grid,
@@ -664,12 +707,100 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
             ws.grow_shift++;
             continue;
         }
-        rc = ws.ensure_queue((uint32_t)cfg.bmax, ws.rings.nch, warps, ws.hv.nslot, stream, g->sms);
+        rc = ws.ensure_queue(nr, ws.rings.nch, warps, stream, g->sms);
         cudaStreamSynchronize(stream);
         if (hc.error == kErrOverflow) return SSSP_E_NOMEM;
         if (hc.error == kErrTimeout) return SSSP_E_TIMEOUT;
         return SSSP_E_CUDA;
     }
+}
+
+// Builds the device layout with shadow vertices for vertices above `split`
+// arcs.  rp0/adj0 are the validated original arrays (device); on success
+// g->row_ptr / g->adj / g->owner describe the layout (rp0/adj0 are freed
+// when new arrays replaced them).
+static int build_layout(Graph* g, int32_t* rp0, uint2* adj0, int32_t split, cudaStream_t s) {
+    const int32_t n = g->n;
+    std::vector<int32_t> h(n + 1);
+    if (cudaMemcpyAsync(h.data(), rp0, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return SSSP_E_CUDA;
+    int64_t ns = 0;
+    for (int32_t v = 0; v < n; v++) {
+        int64_t d = h[v + 1] - h[v];
+        if (split > 0 && d > split) ns += (d + split - 1) / split;
+    }
+    if (ns == 0 || (int64_t)n + ns > 2147483647LL || g->m + ns > 2147483647LL) {
+        g->row_ptr = rp0;
+        g->adj = adj0;
+        g->owner = nullptr;
+        g->nv = n;
+        g->mv = g->m;
+        g->split = 0;
+        return SSSP_OK;
+    }
+    const int32_t nv = (int32_t)(n + ns);
+    std::vector<int32_t> rp1((size_t)nv + 1), sfirst(n, -1), owner((size_t)ns);
+    // real vertices first, then the shadows in vertex order
+    int64_t pos = 0;
+    int32_t next_shadow = n;
+    std::vector<int32_t> sdeg;
+    sdeg.reserve((size_t)ns);
+    for (int32_t v = 0; v < n; v++) {
+        rp1[v] = (int32_t)pos;
+        int64_t d = h[v + 1] - h[v];
+        if (split > 0 && d > split) {
+            int32_t k = (int32_t)((d + split - 1) / split);
+            sfirst[v] = next_shadow;
+            for (int32_t j = 0; j < k; j++) {
+                owner[(size_t)(next_shadow - n) + j] = v;
+                sdeg.push_back((int32_t)std::min<int64_t>(split, d - (int64_t)j * split));
+            }
+            next_shadow += k;
+            pos += k;
+        } else {
+            pos += d;
+        }
+    }
+    for (int64_t i = 0; i < ns; i++) {
+        rp1[(size_t)n + i] = (int32_t)pos;
+        pos += sdeg[(size_t)i];
+    }
+    rp1[nv] = (int32_t)pos;
+    const int64_t mv = pos;
+    int32_t *d_rp1 = nullptr, *d_sfirst = nullptr, *d_owner = nullptr;
+    uint2* d_adj1 = nullptr;
+    int rc = SSSP_OK;
+    if (cudaMalloc(&d_rp1, sizeof(int32_t) * ((size_t)nv + 1)) != cudaSuccess ||
+        cudaMalloc(&d_sfirst, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&d_owner, sizeof(int32_t) * (size_t)ns) != cudaSuccess ||
+        cudaMalloc(&d_adj1, sizeof(uint2) * (size_t)mv) != cudaSuccess) {
+        cudaGetLastError();
+        rc = SSSP_E_NOMEM;
+    }
+    if (rc == SSSP_OK) {
+        cudaMemcpyAsync(d_rp1, rp1.data(), sizeof(int32_t) * ((size_t)nv + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_sfirst, sfirst.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_owner, owner.data(), sizeof(int32_t) * (size_t)ns, cudaMemcpyHostToDevice, s);
+        relayout_kernel<<<g->sms * 8, 256, 0, s>>>(rp0, adj0, n, d_rp1, d_sfirst, split, d_adj1);
+        if (cudaStreamSynchronize(s) != cudaSuccess) rc = SSSP_E_CUDA;
+    }
+    cudaFree(d_sfirst);
+    if (rc != SSSP_OK) {
+        cudaFree(d_rp1);
+        cudaFree(d_owner);
+        cudaFree(d_adj1);
+        return rc;
+    }
+    cudaFree(rp0);
+    cudaFree(adj0);
+    g->row_ptr = d_rp1;
+    g->adj = d_adj1;
+    g->owner = d_owner;
+    g->nv = nv;
+    g->mv = mv;
+    g->split = split;
+    return SSSP_OK;
 }
 
 }  // namespace sssp
@@ -706,6 +837,8 @@ extern "C" int sssp_graph_create(const int32_t* row_ptr, const int32_t* col_idx,
     int rc = SSSP_OK;
     int32_t* col_tmp = nullptr;
     uint32_t* w_tmp = nullptr;
+    int32_t* rp0 = nullptr;
+    uint2* adj0 = nullptr;
     int* flags = nullptr;
     FeatAcc* facc = nullptr;
     FeatAcc hacc;
@@ -713,12 +846,12 @@ extern "C" int sssp_graph_create(const int32_t* row_ptr, const int32_t* col_idx,
     cudaError_t e;
     do {
         if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_status(e); break; }
-        if ((e = cudaMalloc(&g->row_ptr, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess) { rc = cuda_status(e); break; }
-        if ((e = cudaMalloc(&g->adj, sizeof(uint2) * std::max<size_t>((size_t)m, 1))) != cudaSuccess) { rc = cuda_status(e); break; }
+        if ((e = cudaMalloc(&rp0, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess) { rc = cuda_status(e); break; }
+        if ((e = cudaMalloc(&adj0, sizeof(uint2) * std::max<size_t>((size_t)m, 1))) != cudaSuccess) { rc = cuda_status(e); break; }
         if ((e = cudaMalloc(&flags, sizeof(int))) != cudaSuccess) { rc = cuda_status(e); break; }
         if ((e = cudaMalloc(&facc, sizeof(FeatAcc))) != cudaSuccess) { rc = cuda_status(e); break; }
         cudaMemsetAsync(flags, 0, sizeof(int), s);
-        cudaMemcpyAsync(g->row_ptr, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDefault, s);
+        cudaMemcpyAsync(rp0, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDefault, s);
         const int32_t* col_d = col_idx;
         const uint32_t* w_d = (const uint32_t*)weights;
         if (m > 0) {
@@ -733,19 +866,23 @@ extern "C" int sssp_graph_create(const int32_t* row_ptr, const int32_t* col_idx,
                 w_d = w_tmp;
             }
         }
-        validate_rows_kernel<<<grid_for((size_t)n + 1, g->sms), 256, 0, s>>>(g->row_ptr, n, m, flags);
+        validate_rows_kernel<<<grid_for((size_t)n + 1, g->sms), 256, 0, s>>>(rp0, n, m, flags);
         if (m > 0)
             pack_kernel<<<grid_for((size_t)m, g->sms), 256, 0, s>>>(col_d, w_d, m, n, wtype == SSSP_W_F32,
-                                                                  g->adj, flags);
+                                                                  adj0, flags);
         cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { rc = cuda_status(e); break; }
+        cudaFree(col_tmp);
+        cudaFree(w_tmp);
+        col_tmp = nullptr;
+        w_tmp = nullptr;
         if (hflags) { rc = SSSP_E_BADGRAPH; break; }
         FeatAcc init;
         std::memset(&init, 0, sizeof(init));
         init.minw_bits = 0xffffffffu;
         cudaMemcpyAsync(facc, &init, sizeof(init), cudaMemcpyHostToDevice, s);
         features_kernel<<<grid_for((size_t)std::max<int64_t>(n, m), g->sms), 256, 0, s>>>(
-            g->row_ptr, n, g->adj, m, wtype == SSSP_W_F32, facc);
+            rp0, n, adj0, m, wtype == SSSP_W_F32, facc);
         cudaMemcpyAsync(&hacc, facc, sizeof(FeatAcc), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { rc = cuda_status(e); break; }
         sssp_features& f = g->feat;
@@ -772,6 +909,12 @@ extern "C" int sssp_graph_create(const int32_t* row_ptr, const int32_t* col_idx,
         }
         f.symmetric = -1;
         f.has_zero_w = hacc.zero_w ? 1 : 0;
+        rc = build_layout(g, rp0, adj0, 1024, s);
+        f.shadows = g->nv - g->n;
+        if (rc == SSSP_OK) {
+            rp0 = nullptr;  // owned by the graph now (or freed by the relayout)
+            adj0 = nullptr;
+        }
     } while (0);
     cudaFree(col_tmp);
     cudaFree(w_tmp);
@@ -779,8 +922,8 @@ extern "C" int sssp_graph_create(const int32_t* row_ptr, const int32_t* col_idx,
     cudaFree(facc);
     if (s) cudaStreamDestroy(s);
     if (rc != SSSP_OK) {
-        cudaFree(g->row_ptr);
-        cudaFree(g->adj);
+        cudaFree(rp0);
+        cudaFree(adj0);
         delete g;
         return rc;
     }
@@ -797,6 +940,7 @@ extern "C" int sssp_graph_destroy(sssp_graph* gh) {
         g->ws.release();
         cudaFree(g->row_ptr);
         cudaFree(g->adj);
+        cudaFree(g->owner);
     }
     delete g;
     return SSSP_OK;

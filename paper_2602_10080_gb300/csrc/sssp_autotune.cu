@@ -8,7 +8,8 @@
 //       bucket queue when large; meshes: L1FQ-L2V; power-law: priority-aware
 //       L1 over the bucket queue), and
 //   (2) a short timed coordinate search around the prior on sample sources:
-//       L1 policy, delta, bnum, heavy-vertex threshold and block size, each
+//       L1 policy, delta, near window, bnum, shards, claim size, batch size
+//       and block size, each
 //       candidate timed by the CUDA-event duration of the relaxation kernel.
 // The winner is cached on the graph and used by solves given cfg == NULL.
 #include <algorithm>
@@ -37,34 +38,30 @@ sssp_config prior_config(const Graph* g) {
     const sssp_features& f = g->feat;
     switch (family_of(f)) {
         case kPowerLaw:
+            // priority matters most (Section 5.4): filtered L1 over the bucket queue
             c.l1_type = SSSP_L1_FILTER;
             c.l2_type = SSSP_L2_BUCKET;
-            c.filter_deltas = 2.0f;
-            c.bnum = 4;
-            c.bmax = 32;
+            c.filter_deltas = 1.0f;
+            c.near_deltas = 1.0f;
+            c.bnum = 2;
             break;
         case kMesh:
             c.l1_type = SSSP_L1_FILTER;
             c.l2_type = SSSP_L2_BUCKET;
-            c.filter_deltas = 4.0f;
-            c.bnum = 8;
-            c.bmax = 32;
+            c.filter_deltas = 2.0f;
+            c.near_deltas = 2.0f;
+            c.bnum = 4;
             break;
         case kRoad:
-            if (f.n < 500000) {
-                c.l1_type = SSSP_L1_VECTOR;
-                c.wb = 16;
-                c.l2_type = SSSP_L2_BUCKET;
-                c.bnum = 8;
-            } else {
-                c.l1_type = SSSP_L1_VECTOR;
-                c.wb = 8;
-                c.l2_type = SSSP_L2_BUCKET;
-                c.bnum = 4;
-            }
-            c.bmax = 32;
+            // high diameter: wide near window, vector L1, bucket L2 for large graphs
+            c.l1_type = SSSP_L1_VECTOR;
+            c.wb = 0;
+            c.l2_type = SSSP_L2_BUCKET;
+            c.near_deltas = 4.0f;
+            c.bnum = 4;
             break;
     }
+    c.bmax = 32;
     c.delta_u32 = 0;
     c.delta_f32 = 0.0f;
     resolve_auto(g, &c);
@@ -129,7 +126,7 @@ extern "C" int sssp_autotune(sssp_graph* gh, const int32_t* srcs, int32_t nsrc, 
         std::vector<sssp_config> cands;
         // L1 policy (Table 1), with the L1V flush period
         for (int l1 = 0; l1 < 4; l1++) {
-            for (int wb : {0, 8, 32}) {
+            for (int wb : {0, 16}) {
                 if (l1 != SSSP_L1_VECTOR && wb) continue;
                 sssp_config c = best;
                 c.l1_type = l1;
@@ -138,7 +135,7 @@ extern "C" int sssp_autotune(sssp_graph* gh, const int32_t* srcs, int32_t nsrc, 
             }
         }
         // delta (bucket width) and the L2 policy
-        for (double mult : {0.25, 0.5, 2.0, 4.0, 16.0}) {
+        for (double mult : {0.25, 0.5, 2.0, 4.0}) {
             sssp_config c = best;
             if (f32) c.delta_f32 = (float)(d0 * mult);
             else c.delta_u32 = (uint32_t)std::max(1.0, std::round(d0 * mult));
@@ -147,25 +144,37 @@ extern "C" int sssp_autotune(sssp_graph* gh, const int32_t* srcs, int32_t nsrc, 
         {
             sssp_config c = best;
             c.l2_type = SSSP_L2_VECTOR;
-            c.bmax = 1;
-            c.bnum = 1;
             cands.push_back(c);
         }
-        for (int bn : {1, 2, 8, 16}) {
+        for (float nd : {0.0f, 0.5f, 2.0f, 8.0f}) {
             sssp_config c = best;
-            if (c.bmax < bn) continue;
+            c.near_deltas = nd;
+            cands.push_back(c);
+        }
+        for (int bn : {1, 4, 8}) {
+            sssp_config c = best;
             c.bnum = bn;
             cands.push_back(c);
         }
-        for (float fd : {1.0f, 4.0f, 8.0f}) {
+        for (float fd : {0.5f, 2.0f, 4.0f}) {
             sssp_config c = best;
             if (c.l1_type != SSSP_L1_FILTER) continue;
             c.filter_deltas = fd;
             cands.push_back(c);
         }
-        for (int th : {512, 8192}) {
+        for (int sh : {2, 16}) {
             sssp_config c = best;
-            c.th_heavy = th;
+            c.shards = sh;
+            cands.push_back(c);
+        }
+        for (int cl : {1, 8}) {
+            sssp_config c = best;
+            c.claim = cl;
+            cands.push_back(c);
+        }
+        for (int ma : {512, 8192}) {
+            sssp_config c = best;
+            c.max_arcs = ma;
             cands.push_back(c);
         }
         for (int bt : {256, 1024}) {

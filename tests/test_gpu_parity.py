@@ -98,17 +98,26 @@ def test_rmat_f32_exact_and_close_to_f64():
         assert rel.max() <= 1e-6
 
 
-def test_heavy_vertex_tasks():
-    """A hub of degree 200k is split into arc-range tasks across warps."""
+def test_heavy_vertex_shadows():
+    """Hubs (degree 200k and 3000) are split into shadow vertices at creation;
+    their arcs are relaxed by many warps through the ordinary queues."""
     n = 200_001
     edges = [(0, v, (v * 7919) % 1000 + 1) for v in range(1, n)]
     edges += [(v, v + 1, 3) for v in range(1, n - 1)]
+    edges += [(777, v, 1 + v % 13) for v in range(1000, 4000)]
     g = gg.from_edges(n, edges)
     G = upload(g)
-    for th in (256, 4096):
-        d, p = gpu_solve(G, 0, pred=True, config=cfg(th_heavy=th, split=512))
-        assert_exact(g, 0, d, p)
-        assert G.stats()["heavy_tasks"] > 0
+    assert G.features()["shadows"] == 196 + 3
+    for src in (0, 777, 5):
+        for ma in (32, 4096):
+            d, p = gpu_solve(G, src, pred=True, config=cfg(max_arcs=ma))
+            assert_exact(g, src, d, p)
+            d2, _ = gpu_solve(G, src, pred=False, config=cfg(max_arcs=ma, near_deltas=0.0))
+            np.testing.assert_array_equal(d2, d)
+    # batch on the split layout (query slices are padded with shadow vertices)
+    db, pb = gpu_batch(G, np.array([0, 777, 5, 0], np.int32), pred=True)
+    for q, s in enumerate([0, 777, 5, 0]):
+        assert_exact(g, s, db[q], pb[q])
 
 
 @pytest.mark.parametrize("wt", ["u32", "f32"])
