@@ -222,6 +222,44 @@ SSSP_API int sssp_last_stats(const sssp_graph *g, sssp_stats *out);
 SSSP_API int sssp_autotune(sssp_graph *g, const int32_t *srcs, int32_t nsrc, int32_t budget_ms,
                   sssp_config *out);
 
+/* ---------------------------------------------------------- no allocation -- */
+
+/* Largest vertex count sssp_solve_noalloc accepts. */
+#define SSSP_NOALLOC_MAX_VERTICES 2097152
+
+/* Single-source solve that allocates nothing.  The paper has no counterpart;
+ * this entry point exists for callers that cannot allocate device memory at
+ * the time they need an answer: code whose device memory is owned by a pool
+ * or arena, components with an allocation budget fixed up front, and
+ * latency-critical paths that must not call cudaMalloc/cudaFree because
+ * those calls can synchronise the device.
+ *
+ * It runs the same persistent relaxation kernel as sssp_solve with a fixed
+ * configuration (L1 filter queue, 8-bucket L2, no hub splitting), keeping
+ * every piece of scratch state (control block, L2 rings, packed
+ * distance/predecessor words) in one array of about 25 MiB that is part of
+ * the library image: every GPU that loads the library holds it until the
+ * process exits.  The first call on a device sets that array up (resolving
+ * its device address and emptying the queue metadata), so make the first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents; each call re-initialises what must start empty.
+ * Calls serialise on a process-wide lock and return only after the GPU work
+ * has finished; two calls that overlapped on the GPU would race on the array.
+ *
+ *   row_ptr   int32[n + 1], device memory.
+ *   arcs      device memory, 2 * m uint32 words: for arc e, arcs[2e] is the
+ *             column (int32, 0 <= col < n) and arcs[2e + 1] the weight
+ *             (uint32 value or fp32 bits per `wtype`); read only.
+ *   n         1 <= n <= SSSP_NOALLOC_MAX_VERTICES; larger graphs: SSSP_E_INVAL.
+ *   dist_out  n elements, device memory; pred_out n int32, device memory or NULL.
+ *   stream    cudaStream_t or NULL.
+ * The CSR is validated on the device (SSSP_E_BADGRAPH).  Distances and
+ * predecessors follow the conventions of sssp_solve.  SSSP_E_NOMEM if the
+ * fixed L2 rings overflow; host pointers are rejected with SSSP_E_INVAL. */
+SSSP_API int sssp_solve_noalloc(const int32_t *row_ptr, const uint32_t *arcs, int32_t n, int64_t m,
+                                int32_t wtype, int32_t src, void *dist_out, int32_t *pred_out,
+                                void *stream);
+
 /* ---------------------------------------------------------------- serving -- */
 
 /* A serving loop with continuous batching: graphs stay resident; queries

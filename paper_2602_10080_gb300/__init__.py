@@ -22,6 +22,7 @@ SSSP_E_BADGRAPH = -5
 SSSP_E_BUSY = -6
 SSSP_E_NODEV = -7
 SSSP_E_NOTFOUND = -8
+SSSP_NOALLOC_MAX_VERTICES = 2097152
 
 SSSP_W_U32 = 0
 SSSP_W_F32 = 1
@@ -118,6 +119,7 @@ def lib():
         "sssp_serve_wait": (ctypes.c_int, [P, ctypes.c_uint64, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "sssp_serve_latency_us": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
         "sssp_serve_destroy": (ctypes.c_int, [P]),
+        "sssp_solve_noalloc": (ctypes.c_int, [P, P, I32, I64, I32, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -210,6 +212,14 @@ def sssp_autotune(h, srcs=None, budget_ms: int = 0) -> sssp_config:
     nsrc = 0 if srcs is None else int(srcs.numel() if hasattr(srcs, "numel") else srcs.size)
     _check(lib().sssp_autotune(h, _ptr(srcs), nsrc, int(budget_ms), ctypes.byref(c)), "sssp_autotune")
     return c
+
+
+def sssp_solve_noalloc(row_ptr, arcs, n: int, m: int, wtype: int, src: int, dist_out, pred_out=None,
+                       stream=None) -> None:
+    """Single-source solve with no allocation (all arrays device memory; `arcs`
+    holds (column, weight bits) uint32 pairs)."""
+    _check(lib().sssp_solve_noalloc(_ptr(row_ptr), _ptr(arcs), int(n), int(m), int(wtype), int(src),
+                                    _ptr(dist_out), _ptr(pred_out), _stream_ptr(stream)), "sssp_solve_noalloc")
 
 
 def sssp_serve_create(mem_budget_bytes: int, max_slots: int, max_vertices: int):
