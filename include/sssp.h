@@ -71,6 +71,7 @@ extern "C" {
 #define SSSP_E_BUSY      -6 /* serving: no free slot or memory budget right now */
 #define SSSP_E_NODEV     -7 /* no usable CUDA device */
 #define SSSP_E_NOTFOUND  -8 /* serving: unknown ticket */
+#define SSSP_E_CANCELLED -9 /* serving: the query was cancelled */
 
 /* Message for a status code (static string, never NULL). */
 SSSP_API const char *sssp_strerror(int status);
@@ -262,44 +263,110 @@ SSSP_API int sssp_solve_noalloc(const int32_t *row_ptr, const uint32_t *arcs, in
 
 /* ---------------------------------------------------------------- serving -- */
 
-/* A serving loop with continuous batching: graphs stay resident; queries
- * are admitted while earlier ones run, as query slots and the device-memory
- * budget allow, and run in one persistent launch.  (North-star extension;
- * the paper has no serving mode.)
- *   mem_budget_bytes  device bytes for per-query dist/pred/queue state
- *                     (0 = 25% of free device memory).
- *   max_slots         concurrent queries (1..1024).
- *   max_vertices      largest graph n that will be submitted. */
-SSSP_API int sssp_serve_create(size_t mem_budget_bytes, int32_t max_slots, int32_t max_vertices,
-                      sssp_server **out);
+/* Serving with continuous batching.  (An extension: the paper solves one
+ * source per launch and has no serving mode.)  Graphs stay resident; each
+ * graph (and predecessor mode) in use gets a "lane": one multi-query
+ * worklist, per-query distance slices and its own L2 rings.  A worker
+ * thread runs every lane in time slices of slice_us: at the end of a slice
+ * the kernel drains its L0/L1/staging queues into the L2 rings, the host
+ * counts each query's remaining L2 elements, hands finished queries'
+ * results to their buffers and frees their slots, and admits queued
+ * queries into free slots before the next slice -- so new queries join
+ * while earlier ones are still running.  A query admitted while the
+ * lane's bucket window is at W has its buckets shifted by W, so its work
+ * is ordered with the work already in flight.  Lanes of different graphs
+ * run concurrently on their own streams, sharing the SMs. */
+typedef struct sssp_serve_options {
+    size_t  mem_budget_bytes;  /* device bytes for distance slices and L2 rings of all lanes
+                                  (0 = a quarter of the free device memory at creation) */
+    int32_t max_slots;         /* concurrent queries per lane, 1..4096 (default 256); also
+                                  bounded by 2^32 / (vertices rounded up to a power of two) */
+    int32_t slice_us;          /* length of one slice, 50..100000 (default 1000) */
+    int32_t max_queued;        /* queries waiting for a slot; beyond it submit returns
+                                  SSSP_E_BUSY (default 65536) */
+    int32_t ring_shift;        /* initial L2 ring capacity per lane: (slots x vertices) >>
+                                  ring_shift chunks, 0..16 (default 4); rings grow between slices
+                                  when they are half full, and after an overflow the lane's
+                                  queries restart on larger rings */
+    int32_t query_timeout_ms;  /* a query still running after this ends with SSSP_E_TIMEOUT
+                                  (0 = no limit) */
+    int32_t flags;             /* SSSP_SERVE_* test flags below (default 0) */
+    int32_t reserved[2];       /* must be zero */
+} sssp_serve_options;
 
-/* Queues one query.  dist_out / pred_out (pred may be NULL) must stay valid
- * until sssp_serve_poll reports DONE or ERROR; they may be host or device
- * memory.  *ticket_out identifies the query.  SSSP_E_INVAL for a bad
- * graph/source, SSSP_E_BUSY if the host-side queue is full. */
+/* Test flags of sssp_serve_options.flags.  They exercise recovery paths
+ * from the host side; no device fault is involved. */
+#define SSSP_SERVE_MIGRATE_EACH_SLICE 1  /* move the live L2 chunks to new rings after every slice */
+#define SSSP_SERVE_INJECT_OVERFLOW    2  /* treat each lane's first slice as an L2 overflow: the
+                                            lane's queries restart on larger rings */
+#define SSSP_SERVE_INJECT_TIMEOUT     4  /* treat each lane's first slice as a timed-out device
+                                            wait: the lane's queries fail with SSSP_E_TIMEOUT */
+
+typedef struct sssp_serve_stats {
+    int64_t submitted;
+    int64_t completed;         /* DONE */
+    int64_t failed;            /* ERROR, cancellations included */
+    int64_t cancelled;
+    int64_t slices;            /* serving launches (one per lane per slice) */
+    int64_t joined_running;    /* queries admitted into a lane that had queries running */
+    int64_t ring_growths;      /* ring migrations between slices (to larger rings; every slice
+                                  with SSSP_SERVE_MIGRATE_EACH_SLICE) */
+    int64_t restarts;          /* lane restarts after an L2 overflow inside a slice */
+    int64_t max_resident;      /* most queries resident in lanes at once */
+    double  kernel_ms;         /* summed slice kernel time over all lanes */
+} sssp_serve_stats;
+
+/* Fills *opt with the defaults.  SSSP_E_INVAL if opt is NULL. */
+SSSP_API int sssp_serve_options_default(sssp_serve_options *opt);
+
+/* Starts a server on the current device (opt NULL = defaults).
+ * SSSP_E_INVAL for out-of-range options, SSSP_E_NODEV, SSSP_E_CUDA. */
+SSSP_API int sssp_serve_create(const sssp_serve_options *opt, sssp_server **out);
+
+/* Queues one query from `src` on g.  dist_out ([n] distance words as in
+ * sssp_solve) and pred_out ([n], may be NULL) may be host or device memory
+ * and must stay valid until the query is DONE or ERROR; g must not be
+ * destroyed before then.  *ticket_out identifies the query.  SSSP_E_INVAL
+ * for NULL arguments or a source out of range, SSSP_E_BUSY when max_queued
+ * queries are waiting. */
 SSSP_API int sssp_serve_submit(sssp_server *s, sssp_graph *g, int32_t src, void *dist_out,
-                      int32_t *pred_out, uint64_t *ticket_out);
+                               int32_t *pred_out, uint64_t *ticket_out);
 
-/* Query states reported by sssp_serve_poll. */
+/* Query states. */
 #define SSSP_Q_QUEUED  0
 #define SSSP_Q_RUNNING 1
 #define SSSP_Q_DONE    2
 #define SSSP_Q_ERROR   3
 
-/* Non-blocking state of a ticket.  After DONE/ERROR is reported once the
- * ticket is retired (a later poll returns SSSP_E_NOTFOUND).  For ERROR,
- * *status_out (may be NULL) receives the failing SSSP_E_* code. */
+/* Non-blocking state of a ticket; for ERROR, *status_out (may be NULL)
+ * receives the failing SSSP_E_* code (SSSP_E_CANCELLED after a cancel).
+ * Tickets stay known until sssp_serve_release.  SSSP_E_NOTFOUND for an
+ * unknown ticket. */
 SSSP_API int sssp_serve_poll(sssp_server *s, uint64_t ticket, int32_t *state_out, int32_t *status_out);
 
-/* Blocks until the ticket is DONE/ERROR or timeout_ms passes (then
- * SSSP_E_TIMEOUT with the query still live). */
+/* Blocks until the ticket is DONE or ERROR, or timeout_ms passes (then
+ * SSSP_E_TIMEOUT with the query still live; timeout_ms < 0 waits forever). */
 SSSP_API int sssp_serve_wait(sssp_server *s, uint64_t ticket, int32_t timeout_ms, int32_t *state_out,
-                    int32_t *status_out);
+                             int32_t *status_out);
 
-/* Submit-to-done latency of the ticket's query in microseconds (valid after DONE). */
+/* Submit-to-DONE latency of the ticket in microseconds; SSSP_E_BUSY while
+ * the query is not DONE. */
 SSSP_API int sssp_serve_latency_us(sssp_server *s, uint64_t ticket, double *us_out);
 
-/* Stops the loop (waits for queries in flight) and frees the server. */
+/* Cancels a queued or running query: SSSP_OK means it ended with
+ * ERROR/SSSP_E_CANCELLED and its buffers are not written after the call
+ * returns; SSSP_E_BUSY means its results are already being delivered (it
+ * will be DONE); SSSP_E_INVAL if it had already ended.  A running query's
+ * slot is reused once its remaining queue elements have drained. */
+SSSP_API int sssp_serve_cancel(sssp_server *s, uint64_t ticket);
+
+/* Forgets a DONE/ERROR ticket (SSSP_E_BUSY while it is queued or running). */
+SSSP_API int sssp_serve_release(sssp_server *s, uint64_t ticket);
+
+/* Counters since creation. */
+SSSP_API int sssp_serve_get_stats(sssp_server *s, sssp_serve_stats *out);
+
+/* Lets every queued and running query finish, then frees the server. */
 SSSP_API int sssp_serve_destroy(sssp_server *s);
 
 #ifdef __cplusplus

@@ -22,6 +22,7 @@ SSSP_E_BADGRAPH = -5
 SSSP_E_BUSY = -6
 SSSP_E_NODEV = -7
 SSSP_E_NOTFOUND = -8
+SSSP_E_CANCELLED = -9
 SSSP_NOALLOC_MAX_VERTICES = 2097152
 
 SSSP_W_U32 = 0
@@ -29,6 +30,7 @@ SSSP_W_F32 = 1
 L1_VECTOR, L1_NEARFAR, L1_FILTER, L1_SLF = 0, 1, 2, 3
 L2_VECTOR, L2_BUCKET = 0, 1
 Q_QUEUED, Q_RUNNING, Q_DONE, Q_ERROR = 0, 1, 2, 3
+SERVE_MIGRATE_EACH_SLICE, SERVE_INJECT_OVERFLOW, SERVE_INJECT_TIMEOUT = 1, 2, 4
 
 
 class SsspError(RuntimeError):
@@ -50,6 +52,26 @@ class sssp_config(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class sssp_serve_options(ctypes.Structure):
+    _fields_ = [
+        ("mem_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("slice_us", ctypes.c_int32),
+        ("max_queued", ctypes.c_int32), ("ring_shift", ctypes.c_int32), ("query_timeout_ms", ctypes.c_int32),
+        ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+    ]
+
+
+class sssp_serve_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+        ("cancelled", ctypes.c_int64), ("slices", ctypes.c_int64), ("joined_running", ctypes.c_int64),
+        ("ring_growths", ctypes.c_int64), ("restarts", ctypes.c_int64), ("max_resident", ctypes.c_int64),
+        ("kernel_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class sssp_features(ctypes.Structure):
@@ -113,11 +135,15 @@ def lib():
         "sssp_solve_batch": (ctypes.c_int, [P, P, I32, P, P, ctypes.POINTER(sssp_config), P]),
         "sssp_last_stats": (ctypes.c_int, [P, ctypes.POINTER(sssp_stats)]),
         "sssp_autotune": (ctypes.c_int, [P, P, I32, I32, ctypes.POINTER(sssp_config)]),
-        "sssp_serve_create": (ctypes.c_int, [ctypes.c_size_t, I32, I32, ctypes.POINTER(P)]),
+        "sssp_serve_options_default": (ctypes.c_int, [ctypes.POINTER(sssp_serve_options)]),
+        "sssp_serve_create": (ctypes.c_int, [ctypes.POINTER(sssp_serve_options), ctypes.POINTER(P)]),
         "sssp_serve_submit": (ctypes.c_int, [P, P, I32, P, P, ctypes.POINTER(ctypes.c_uint64)]),
         "sssp_serve_poll": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "sssp_serve_wait": (ctypes.c_int, [P, ctypes.c_uint64, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "sssp_serve_latency_us": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+        "sssp_serve_cancel": (ctypes.c_int, [P, ctypes.c_uint64]),
+        "sssp_serve_release": (ctypes.c_int, [P, ctypes.c_uint64]),
+        "sssp_serve_get_stats": (ctypes.c_int, [P, ctypes.POINTER(sssp_serve_stats)]),
         "sssp_serve_destroy": (ctypes.c_int, [P]),
         "sssp_solve_noalloc": (ctypes.c_int, [P, P, I32, I64, I32, I32, P, P, P]),
     }
@@ -222,10 +248,21 @@ def sssp_solve_noalloc(row_ptr, arcs, n: int, m: int, wtype: int, src: int, dist
                                     _ptr(dist_out), _ptr(pred_out), _stream_ptr(stream)), "sssp_solve_noalloc")
 
 
-def sssp_serve_create(mem_budget_bytes: int, max_slots: int, max_vertices: int):
+def sssp_serve_options_default() -> sssp_serve_options:
+    o = sssp_serve_options()
+    _check(lib().sssp_serve_options_default(ctypes.byref(o)), "sssp_serve_options_default")
+    return o
+
+
+def sssp_serve_create(opt: sssp_serve_options | None = None, **kw):
+    """Starts a server; `opt` (or keyword overrides of the defaults) as in
+    sssp_serve_options."""
+    if opt is None:
+        opt = sssp_serve_options_default()
+    for k, v in kw.items():
+        setattr(opt, k, v)
     h = ctypes.c_void_p()
-    _check(lib().sssp_serve_create(mem_budget_bytes, max_slots, max_vertices, ctypes.byref(h)),
-           "sssp_serve_create")
+    _check(lib().sssp_serve_create(ctypes.byref(opt), ctypes.byref(h)), "sssp_serve_create")
     return h
 
 
@@ -253,6 +290,21 @@ def sssp_serve_latency_us(s, ticket: int) -> float:
     v = ctypes.c_double()
     _check(lib().sssp_serve_latency_us(s, ticket, ctypes.byref(v)), "sssp_serve_latency_us")
     return v.value
+
+
+def sssp_serve_cancel(s, ticket: int) -> int:
+    """Returns the status code (SSSP_OK, SSSP_E_BUSY or SSSP_E_INVAL) without raising."""
+    return lib().sssp_serve_cancel(s, ticket)
+
+
+def sssp_serve_release(s, ticket: int) -> None:
+    _check(lib().sssp_serve_release(s, ticket), "sssp_serve_release")
+
+
+def sssp_serve_get_stats(s) -> dict:
+    st = sssp_serve_stats()
+    _check(lib().sssp_serve_get_stats(s, ctypes.byref(st)), "sssp_serve_get_stats")
+    return st.as_dict()
 
 
 def sssp_serve_destroy(s) -> None:

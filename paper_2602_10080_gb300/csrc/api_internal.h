@@ -37,6 +37,7 @@ struct Workspace {
 };
 
 struct Graph {
+    uint64_t uid = 0;             // unique per created graph (a handle's address may be reused)
     int device = 0;
     int sms = 1;
     int32_t n = 0;                // real vertices
@@ -57,7 +58,21 @@ struct Graph {
     std::mutex mu;
 };
 
+// Launch shape, shared-memory layout and the graph/config part of the
+// kernel parameters for one instantiation; the caller fills nq, dist,
+// vbits/vmask, l2 and ctrl.
+struct LaunchPlan {
+    KernelKey key;
+    int threads = 0;
+    int bps = 0;       // blocks per SM
+    int grid = 0;      // sms * bps
+    size_t smem = 0;
+    KParams P;
+};
+
 int cuda_status(cudaError_t e);
+int pred_mode_for(const Graph* g);
+int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, LaunchPlan* out);
 bool is_device_ptr(const void* p);
 void resolve_auto(const Graph* g, sssp_config* c);
 int validate_config(const sssp_config* c);

@@ -90,7 +90,8 @@ struct __align__(128) Ctrl {
     int error;
     int err_where;
     int err_info;
-    int pad3[28];
+    unsigned long long slice_end;        // serving: globaltimer value at which the current slice ends (0 = unset)
+    int pad3[26];
     unsigned long long stats[32];
 };
 
@@ -132,6 +133,8 @@ struct KParams {
     int32_t stage;           // 1: heavy-arc writes are pooled per bucket in the block before L2
     int32_t scratch_off, far_off, stat_off, stage_off, l1_off;  // byte offsets in dynamic shared memory
     unsigned long long timeout_ns;
+    unsigned long long slice_ns;   // serving: end the launch after this long, draining local queues to L2 (0 = run to completion)
+    const uint32_t* qoff;          // serving: per-query bucket offset (the window position when the query was admitted), or null
     unsigned long long* trace;   // debug only: per-lane (location << 48 | iteration), mapped host memory
 };
 
@@ -245,6 +248,7 @@ struct BlockShared {
     uint32_t writes;              // L1 write calls (periodic flush)
     unsigned long long acct;      // (held elements << 32) | unpublished L2 reads
     uint32_t scnt[32];            // elements staged per L2 bucket ring index
+    unsigned long long slice_end; // serving: end of this launch's slice (globaltimer), ~0 = none
 };
 
 // ------------------------------------------------------------- watchdog --
@@ -276,6 +280,7 @@ struct Worker {
     DistT* dist;
     uint32_t lane;
     unsigned long long deadline;
+    unsigned long long slice_end;
 
     // L0 ring
     uint2 l0[R];
@@ -290,7 +295,8 @@ struct Worker {
     __device__ Worker(const KParams& p, BlockShared* s, uint2* scr, uint2* far, uint2* stage, uint2* l1,
                       unsigned long long* stats, unsigned long long dl)
         : P(p), S(s), scratch(scr), farbuf(far), stg(stage), L1(l1), dist(reinterpret_cast<DistT*>(p.dist)),
-          lane(lane_id()), deadline(dl), l0h(0), l0t(0), nfar(0), unc(0), dec(0),
+          lane(lane_id()), deadline(dl), slice_end(s->slice_end), l0h(0), l0t(0),
+          nfar(0), unc(0), dec(0),
           sst(stats) {
         if (lane == 0)
             for (int i = 0; i < kStCount; i++) sst[i] = 0;
@@ -424,7 +430,7 @@ struct Worker {
         const uint32_t W = (uint32_t)win;
         const uint32_t shard = home_shard();
         // absolute bucket; beyond the window span -> the window's last bucket
-        uint32_t ab = valid ? A::bucket(e.y, P.delta) : W;
+        uint32_t ab = valid ? abs_bucket(e.x, e.y) : W;
         if (ab > W && ab - W >= (uint32_t)P.bmax) ab = W + (uint32_t)P.bmax - 1u;
         const uint32_t b = ab % (uint32_t)P.bmax;
         const uint32_t below = __reduce_min_sync(kFull, valid ? ab : 0xffffffffu);
@@ -694,7 +700,10 @@ struct Worker {
             // vector (type 0) / filter (type 2, keep dist <= fthr)
 #pragma unroll
             for (int k = 0; k < K; k++) {
-                bool want = valid[k] && (type != 2 || e[k].y <= fthr);
+                // with admission offsets (serving) the filter compares
+                // absolute buckets: fthr then holds the last bucket kept
+                bool want = valid[k] &&
+                            (type != 2 || (MQ && P.qoff ? abs_bucket(e[k].x, e[k].y) <= fthr : e[k].y <= fthr));
                 uint32_t wm = __ballot_sync(kFull, want);
                 uint32_t h = sread(&S->head), t = sread(&S->tail);
                 uint32_t space = cap - (t - h);
@@ -766,7 +775,8 @@ struct Worker {
             unsigned long long win = 0;
             if (lane == 0) win = window();
             win = __shfl_sync(kFull, win, 0);
-            fthr = A::upper((uint32_t)win, P.delta, P.filter_deltas);  // (W + F) * delta
+            fthr = MQ && P.qoff ? (uint32_t)win + (uint32_t)P.filter_deltas       // bucket W + F
+                                : A::upper((uint32_t)win, P.delta, P.filter_deltas);  // (W + F) * delta
         }
         bool out[K];
         if (!lock()) return;
@@ -987,8 +997,16 @@ struct Worker {
     // the window's first two buckets are urgent and go to L2 at once; partial
     // buckets are flushed when they become urgent or the block runs dry.
 
-    __device__ __forceinline__ uint32_t ring_bucket(uint32_t d, uint32_t W, uint32_t& ab) const {
-        ab = A::bucket(d, P.delta);
+    // absolute bucket of an element: floor(d / delta), shifted by the query's
+    // admission offset when queries started at different times (serving)
+    __device__ __forceinline__ uint32_t abs_bucket(uint32_t key, uint32_t d) const {
+        uint32_t ab = A::bucket(d, P.delta);
+        if (MQ && P.qoff) ab += __ldg(P.qoff + key_query(key));
+        return ab;
+    }
+
+    __device__ __forceinline__ uint32_t ring_bucket(uint32_t key, uint32_t d, uint32_t W, uint32_t& ab) const {
+        ab = abs_bucket(key, d);
         if (ab > W && ab - W >= (uint32_t)P.bmax) ab = W + (uint32_t)P.bmax - 1u;
         return ab % (uint32_t)P.bmax;
     }
@@ -1048,7 +1066,7 @@ struct Worker {
                 continue;
             }
             uint32_t ab = 0;
-            const uint32_t b = v ? ring_bucket(x.y, W, ab) : 0u;
+            const uint32_t b = v ? ring_bucket(x.x, x.y, W, ab) : 0u;
             const bool urgent = v && (ab <= W + 1u || key_vertex(x.x) >= (uint32_t)P.n);
             dec += l2_write(urgent, x);
             const bool sv = v && !urgent;
@@ -1271,6 +1289,7 @@ struct Worker {
                         raise_error(P.ctrl, kErrTimeout, 7, 0);
                         stop = 1;
                     }
+                    if (!stop && gtime() > slice_end) stop = 2;  // end of a serving slice
                 }
                 stop = __shfl_sync(kFull, stop, 0);
                 if (stop) break;
@@ -1329,7 +1348,77 @@ struct Worker {
             acct_apply();
         }
         mark(13, iter);
+        drain_warp();
         publish_stats();
+    }
+
+    // End of a launch: move everything this warp holds (L0, far staging) to
+    // L2.  After a normal termination there is nothing left and this is a
+    // no-op; at the end of a serving slice the work continues from L2 in the
+    // next launch.
+    __device__ void drain_warp() {
+        if (ld_volatile_int(&P.ctrl->error) != 0) return;
+        const uint32_t len = l0t - l0h;
+        if (len) {
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const uint32_t want = 32u * (uint32_t)r + lane;
+                const uint32_t p = l0h + ((want - l0h) & (32u * R - 1u));
+                dec += l2_write((p - l0h) < len, l0[r]);
+            }
+            l0h = l0t = 0;
+        }
+        if (nfar) far_flush(0);
+        acct_apply();
+    }
+
+    // End of a launch, one warp per block after every warp drained: move L1
+    // and the block staging to L2, then publish the block's count.
+    __device__ void drain_block() {
+        if (ld_volatile_int(&P.ctrl->error) != 0) return;
+        if (lock()) {
+            if (P.l1_type == 1) {
+                const uint32_t half = (uint32_t)P.l1_cap >> 1;
+                for (int rg = 0; rg < 2; rg++) {
+                    uint32_t* hp = rg ? &S->fhead : &S->head;
+                    uint32_t* tp = rg ? &S->ftail : &S->tail;
+                    uint32_t h = sread(hp), t = sread(tp);
+                    while (h != t) {
+                        const uint32_t c = t - h < 32u ? t - h : 32u;
+                        const bool v = lane < c;
+                        uint2 x = make_uint2(0, 0);
+                        if (v) x = vld(&L1[(rg ? half : 0u) + ((h + lane) & (half - 1u))]);
+                        h += c;
+                        dec += l2_write(v, x);
+                    }
+                    if (lane == 0) *(volatile uint32_t*)hp = h;
+                    __syncwarp();
+                }
+            } else {
+                uint32_t h = sread(&S->head), t = sread(&S->tail);
+                while (h != t) {
+                    const uint32_t c = t - h < 32u ? t - h : 32u;
+                    const bool v = lane < c;
+                    uint2 x = make_uint2(0, 0);
+                    if (v) x = vld(&L1[(h + lane) & l1_mask()]);
+                    h += c;
+                    dec += l2_write(v, x);
+                }
+                if (lane == 0) *(volatile uint32_t*)&S->head = h;
+                __syncwarp();
+            }
+            unlock();
+        }
+        stage_flush(true);
+        acct_apply();
+        if (lane == 0) {
+            // nothing may stay behind in the block: its count must be zero,
+            // and the L2 reads it finished are published to ctrl.done
+            const unsigned long long v = *(volatile unsigned long long*)&S->acct;
+            if ((uint32_t)(v >> 32) != 0u) raise_error(P.ctrl, kErrState, 9, (int)(v >> 32));
+            else try_flush();
+        }
+        __syncwarp();
     }
 };
 
@@ -1351,6 +1440,13 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
         for (int i = 0; i < 32; i++) S->scnt[i] = 0;
         unsigned long long win = ld_acquire64(&P.ctrl->window);
         S->nf = Arith<WT>::upper((uint32_t)win, P.delta, 1.0f);
+        S->slice_end = ~0ull;
+        if (P.slice_ns) {
+            // the first block to start fixes the slice's end for all blocks
+            const unsigned long long mine = gtime() + P.slice_ns;
+            const unsigned long long prev = atomicCAS(&P.ctrl->slice_end, 0ull, mine);
+            S->slice_end = prev ? prev : mine;
+        }
     }
     __syncthreads();
     const unsigned long long deadline = gtime() + P.timeout_ns;
@@ -1358,6 +1454,12 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
     Worker<WT, PRED, MQ, R> w(P, S, scratch_all + warp * 32, far_all + warp * kFarCap, stage, l1,
                               stats_all + warp * kStCount, deadline);
     w.run();
+    if (P.slice_ns) {
+        // serving slice: every warp has drained its private state; one warp
+        // now drains what the block shares
+        __syncthreads();
+        if (warp == 0) w.drain_block();
+    }
 }
 
 }  // namespace sssp

@@ -3,6 +3,7 @@
 // batched solves, statistics.  Autotuning lives in sssp_autotune.cu, serving
 // in sssp_serve.cu.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -455,6 +456,72 @@ int validate_config(const sssp_config* c) {
     return SSSP_OK;
 }
 
+// ================================================================== launch plan
+
+int pred_mode_for(const Graph* g) {
+    // the packed atomicMin keeps the smallest-index tight predecessor when
+    // every weight is >= 1; otherwise strict improvements decide (CAS)
+    return (g->wtype == SSSP_W_U32 && g->feat.min_w >= 1.0) ? 1 : 2;
+}
+
+int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, LaunchPlan* out) {
+    LaunchPlan& L = *out;
+    L.key = KernelKey{g->wtype == SSSP_W_F32 ? 1 : 0, pred_mode, mq ? 1 : 0};
+    // shared-memory layout of one block
+    L.threads = cfg.block_threads;
+    const int warps_per_block = L.threads / 32;
+    const size_t scratch_off = (sizeof(BlockShared) + 15) & ~size_t(15);
+    const size_t far_off = scratch_off + (size_t)warps_per_block * 32 * sizeof(uint2);
+    const size_t stat_off = far_off + (size_t)warps_per_block * kFarCap * sizeof(uint2);
+    const size_t stage_off = stat_off + (size_t)warps_per_block * kStCount * sizeof(unsigned long long);
+    const size_t l1_off = stage_off + (cfg.stage ? (size_t)cfg.bmax * kStageCap * sizeof(uint2) : 0);
+    L.smem = l1_off + (size_t)cfg.l1_cap * sizeof(uint2);
+    int occ = 0;
+    cudaError_t ce = occupancy_mlmq(L.key, L.threads, L.smem, &occ);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    if (occ < 1) return SSSP_E_INVAL;
+    L.bps = cfg.blocks_per_sm > 0 ? std::min(cfg.blocks_per_sm, occ) : occ;
+    L.grid = g->sms * L.bps;
+
+    KParams& P = L.P;
+    std::memset(&P, 0, sizeof(P));
+    P.row_ptr = g->row_ptr;
+    P.adj = g->adj;
+    P.owner = g->owner;
+    P.n = g->n;
+    P.nv = g->nv;
+    P.nq = 1;
+    P.vmask = 0xffffffffu;
+    P.shards = cfg.shards;
+    P.delta = g->wtype == SSSP_W_F32 ? __float_as_uint_host(cfg.delta_f32) : cfg.delta_u32;
+    P.bnum = std::min(cfg.bnum, cfg.bmax);
+    P.bmax = cfg.bmax;
+    P.l1_type = cfg.l1_type;
+    P.l1_cap = cfg.l1_cap;
+    P.wb = cfg.l1_type == SSSP_L1_VECTOR ? cfg.wb : 0;
+    P.filter_deltas = cfg.filter_deltas;
+    if (cfg.near_deltas > 0.0f) {
+        if (g->wtype == SSSP_W_F32)
+            P.near_w = __float_as_uint_host(cfg.delta_f32 * cfg.near_deltas);
+        else
+            P.near_w = (uint32_t)std::min(4294967295.0, (double)cfg.delta_u32 * cfg.near_deltas);
+    } else {
+        P.near_w = kInfU32;   // every write enters L0, as in Listing 1
+    }
+    P.max_arcs = cfg.max_arcs;
+    P.claim = cfg.claim;
+    P.refillers = cfg.refillers;
+    P.scratch_off = (int32_t)scratch_off;
+    P.far_off = (int32_t)far_off;
+    P.stat_off = (int32_t)stat_off;
+    P.stage_off = (int32_t)stage_off;
+    P.stage = cfg.stage ? 1 : 0;
+    P.l1_off = (int32_t)l1_off;
+    const int tmo = cfg.timeout_ms > 0 ? cfg.timeout_ms : 20000;
+    P.timeout_ns = (unsigned long long)tmo * 1000000ull;
+    return SSSP_OK;
+}
+
 // ================================================================== solve
 
 int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int32_t src0, int32_t nq,
@@ -473,26 +540,17 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
         if (vbits == 0) vbits = 1;
         if ((unsigned long long)nq << vbits > (1ull << 32)) return SSSP_E_INVAL;
     }
-    const int pred_mode = pred_out ? ((g->wtype == SSSP_W_U32 && g->feat.min_w >= 1.0) ? 1 : 2) : 0;
-    const KernelKey key{g->wtype == SSSP_W_F32 ? 1 : 0, pred_mode, mq ? 1 : 0};
+    const int pred_mode = pred_out ? pred_mode_for(g) : 0;
+    LaunchPlan plan;
+    rc = plan_launch(g, cfg, pred_mode, mq, &plan);
+    if (rc) return rc;
+    const KernelKey key = plan.key;
     const int shards = cfg.shards;
-
-    // launch shape and shared-memory layout
-    const int threads = cfg.block_threads;
-    const int warps_per_block = threads / 32;
-    const size_t scratch_off = (sizeof(BlockShared) + 15) & ~size_t(15);
-    const size_t far_off = scratch_off + (size_t)warps_per_block * 32 * sizeof(uint2);
-    const size_t stat_off = far_off + (size_t)warps_per_block * kFarCap * sizeof(uint2);
-    const size_t stage_off = stat_off + (size_t)warps_per_block * kStCount * sizeof(unsigned long long);
-    const size_t l1_off = stage_off + (cfg.stage ? (size_t)cfg.bmax * kStageCap * sizeof(uint2) : 0);
-    const size_t smem = l1_off + (size_t)cfg.l1_cap * sizeof(uint2);
-    int occ = 0;
-    cudaError_t ce = occupancy_mlmq(key, threads, smem, &occ);
-    if (ce != cudaSuccess) return cuda_status(ce);
-    if (occ < 1) return SSSP_E_INVAL;
-    const int bps = cfg.blocks_per_sm > 0 ? std::min(cfg.blocks_per_sm, occ) : occ;
-    const int grid = g->sms * bps;
-    const uint32_t warps = (uint32_t)(grid * warps_per_block);
+    const int threads = plan.threads;
+    const int grid = plan.grid;
+    const size_t smem = plan.smem;
+    const uint32_t warps = (uint32_t)(grid * (threads / 32));
+    cudaError_t ce = cudaSuccess;
 
     Workspace& ws = g->ws;
     const size_t cells = (size_t)nq * (size_t)nv;       // work slices
@@ -535,46 +593,14 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
             srcs_d = ws.srcs;
         }
 
-        KParams P;
-        std::memset(&P, 0, sizeof(P));
-        P.row_ptr = g->row_ptr;
-        P.adj = g->adj;
-        P.owner = g->owner;
-        P.n = n;
-        P.nv = nv;
+        KParams P = plan.P;
         P.nq = nq;
         P.dist = work;
         P.vbits = mq ? vbits : 0;
         P.vmask = mq ? ((1u << vbits) - 1u) : 0xffffffffu;
         P.l2 = ws.rings;
-        P.shards = shards;
         P.ctrl = ws.ctrl;
-        P.delta = g->wtype == SSSP_W_F32 ? __float_as_uint_host(cfg.delta_f32) : cfg.delta_u32;
-        P.bnum = std::min(cfg.bnum, cfg.bmax);
-        P.bmax = cfg.bmax;
-        P.l1_type = cfg.l1_type;
-        P.l1_cap = cfg.l1_cap;
-        P.wb = cfg.l1_type == SSSP_L1_VECTOR ? cfg.wb : 0;
-        P.filter_deltas = cfg.filter_deltas;
-        if (cfg.near_deltas > 0.0f) {
-            if (g->wtype == SSSP_W_F32)
-                P.near_w = __float_as_uint_host(cfg.delta_f32 * cfg.near_deltas);
-            else
-                P.near_w = (uint32_t)std::min(4294967295.0, (double)cfg.delta_u32 * cfg.near_deltas);
-        } else {
-            P.near_w = kInfU32;   // every write enters L0, as in Listing 1
-        }
-        P.max_arcs = cfg.max_arcs;
-        P.claim = cfg.claim;
-        P.refillers = cfg.refillers;
-        P.scratch_off = (int32_t)scratch_off;
-        P.far_off = (int32_t)far_off;
-        P.stat_off = (int32_t)stat_off;
-        P.stage_off = (int32_t)stage_off;
-        P.stage = cfg.stage ? 1 : 0;
-        P.l1_off = (int32_t)l1_off;
         const int tmo = cfg.timeout_ms > 0 ? cfg.timeout_ms : 20000;
-        P.timeout_ns = (unsigned long long)tmo * 1000000ull;
 
         cudaEventRecord(ws.ev0, stream);
         if (pred_mode)
@@ -825,8 +851,10 @@ extern "C" int sssp_graph_create(const int32_t* row_ptr, const int32_t* col_idx,
         cudaGetLastError();
         return SSSP_E_NODEV;
     }
+    static std::atomic<uint64_t> next_uid{1};
     Graph* g = new (std::nothrow) Graph();
     if (!g) return SSSP_E_NOMEM;
+    g->uid = next_uid.fetch_add(1);
     cudaGetDevice(&g->device);
     cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device);
     g->n = n;

@@ -94,3 +94,41 @@ def test_bad_arguments_rejected_before_device(lib):
     assert lib.sssp_graph_create(None, None, None, 0, 0, 0, ctypes.byref(h)) == sssp.SSSP_E_INVAL
     assert lib.sssp_solve(None, 0, None, None, None, None) == sssp.SSSP_E_INVAL
     assert lib.sssp_solve_batch(None, None, 0, None, None, None, None) == sssp.SSSP_E_INVAL
+
+
+def test_serve_options_rejected_before_device(lib):
+    o = sssp.sssp_serve_options_default()
+    assert o.max_slots == 256 and o.slice_us == 1000 and o.flags == 0
+    assert lib.sssp_serve_options_default(None) == sssp.SSSP_E_INVAL
+    h = ctypes.c_void_p()
+    for field, value in (("max_slots", 0), ("max_slots", 5000), ("slice_us", 10), ("ring_shift", 17),
+                         ("query_timeout_ms", -1), ("flags", 64), ("max_queued", 0)):
+        bad = sssp.sssp_serve_options_default()
+        setattr(bad, field, value)
+        assert lib.sssp_serve_create(ctypes.byref(bad), ctypes.byref(h)) == sssp.SSSP_E_INVAL, field
+    bad = sssp.sssp_serve_options_default()
+    bad.reserved[0] = 1
+    assert lib.sssp_serve_create(ctypes.byref(bad), ctypes.byref(h)) == sssp.SSSP_E_INVAL
+    assert lib.sssp_serve_create(None, None) == sssp.SSSP_E_INVAL
+    assert lib.sssp_serve_destroy(None) == sssp.SSSP_OK
+    assert lib.sssp_serve_submit(None, None, 0, None, None, None) == sssp.SSSP_E_INVAL
+
+
+def test_serve_struct_layouts_match_c(tmp_path):
+    src = tmp_path / "serve_layout.c"
+    src.write_text(f'''
+#include <stdio.h>
+#include <stddef.h>
+#include "{HEADER}"
+int main(void) {{
+  printf("%zu %zu %zu %zu\\n", sizeof(sssp_serve_options), sizeof(sssp_serve_stats),
+         offsetof(sssp_serve_options, flags), offsetof(sssp_serve_stats, kernel_ms));
+  return 0;
+}}
+''')
+    exe = tmp_path / "serve_layout"
+    subprocess.run(["gcc", str(src), "-o", str(exe)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    assert vals == [ctypes.sizeof(sssp.sssp_serve_options), ctypes.sizeof(sssp.sssp_serve_stats),
+                    sssp.sssp_serve_options.flags.offset, sssp.sssp_serve_stats.kernel_ms.offset]
