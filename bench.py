@@ -183,6 +183,135 @@ def run_reference(args):
     return 0
 
 
+def batch_leg(S, gg, torch, wtype: str = "u32", nq: int = 256, seq_sample: int = 32):
+    """Batched throughput: nq sources of R-MAT 20 in one persistent launch
+    (sssp_solve_batch, dist nq x n on the device) against one-at-a-time
+    sssp_solve calls on the same sources (a timed sample of them)."""
+    g = gg.workload("rmat20" if wtype == "u32" else "rmat20f")
+    srcs, _ = gg.giant_sources(g, nq, seed=2)
+    G = S.Graph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda(),
+                torch.from_numpy(g.w_bits.view(np.int32)).cuda(), g.wtype)
+    try:
+        st = torch.from_numpy(srcs.astype(np.int32)).cuda()
+        out = torch.empty(len(srcs) * g.n, dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream()
+        G.solve_batch(st, out, None, None, stream)           # warm-up
+        torch.cuda.synchronize()
+        reps = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            G.solve_batch(st, out, None, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        batch_s = e0.elapsed_time(e1) / 1e3 / reps
+        one = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for s in srcs[:3]:
+            G.solve(int(s), one, None, None, stream)
+        torch.cuda.synchronize()
+        k = min(seq_sample, len(srcs))
+        e0.record(stream)
+        for s in srcs[:k]:
+            G.solve(int(s), one, None, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_s = e0.elapsed_time(e1) / 1e3 / k
+        return {"workload": f"{'rmat20' if wtype == 'u32' else 'rmat20f'} x{len(srcs)} sources, one launch",
+                "dtype": wtype, "qps": round(len(srcs) / batch_s, 1), "ms_per_batch": round(batch_s * 1e3, 2),
+                "sequential_qps": round(1.0 / seq_s, 1),
+                "sequential_sample": f"{k} sssp_solve calls",
+                "speedup": round(seq_s * len(srcs) / batch_s, 2)}
+    finally:
+        G.close()
+
+
+SERVE_GRAPHS = ("grid1024", "rmat18", "rmat20", "rmat22", "er21")
+
+
+def serve_leg(S, gg, torch, rates, seconds: float, max_queries: int, graph_cache: dict):
+    """Served latency/throughput: Poisson arrivals over the resident graphs
+    (graph uniform per query, source uniform over its giant component),
+    through the continuous-batching server, and the same arrival trace
+    through a one-at-a-time sssp_solve loop (FIFO)."""
+    graphs = []
+    for name in SERVE_GRAPHS:
+        if name not in graph_cache:
+            g = gg.workload(name)
+            G = S.Graph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda(),
+                        torch.from_numpy(g.w_bits.view(np.int32)).cuda(), g.wtype)
+            srcs, _ = gg.giant_sources(g, 4096, seed=2)
+            graph_cache[name] = (g, G, srcs)
+        graphs.append(graph_cache[name])
+    nbuf = 64
+    bufs = [[torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(nbuf)] for g, _, _ in graphs]
+    out = []
+    for ri, rate in enumerate(rates):
+        count = int(max(20, min(max_queries, rate * seconds)))
+        arr = gg.poisson_arrivals(rate, count, seed=3, stream=8 + ri)
+        ug = gg.uniform_stream(3, 20 + ri, count)
+        us = gg.uniform_stream(3, 40 + ri, count)
+        trace = []
+        for i in range(count):
+            gi = min(int(ug[i] * len(graphs)), len(graphs) - 1)
+            srcs = graphs[gi][2]
+            trace.append((float(arr[i]), gi, int(srcs[min(int(us[i] * len(srcs)), len(srcs) - 1)])))
+        # --- served
+        srv = S.sssp_serve_create(slice_us=500)
+        try:
+            # warm the lanes (allocation, first launch) outside the trace
+            warm = [S.sssp_serve_submit(srv, G.handle, int(srcs[0]), bufs[gi][0], None)
+                    for gi, (_, G, srcs) in enumerate(graphs)]
+            for t in warm:
+                S.sssp_serve_wait(srv, t, -1)
+            last_ticket = [[None] * nbuf for _ in graphs]
+            used = [0] * len(graphs)
+            tickets = []
+            t0 = time.perf_counter()
+            for at, gi, src in trace:
+                now = time.perf_counter() - t0
+                if at > now:
+                    time.sleep(at - now)
+                slot = used[gi] % nbuf
+                used[gi] += 1
+                if last_ticket[gi][slot] is not None:      # buffer still in use
+                    S.sssp_serve_wait(srv, last_ticket[gi][slot], -1)
+                t = S.sssp_serve_submit(srv, graphs[gi][1].handle, src, bufs[gi][slot], None)
+                last_ticket[gi][slot] = t
+                tickets.append(t)
+            for t in tickets:
+                st, code = S.sssp_serve_wait(srv, t, -1)
+                if st != S.Q_DONE:
+                    raise RuntimeError(f"served query failed: {S.strerror(code)}")
+            t_end = time.perf_counter() - t0
+            lat = np.array([S.sssp_serve_latency_us(srv, t) for t in tickets]) / 1e3
+            sstats = S.sssp_serve_get_stats(srv)
+        finally:
+            S.sssp_serve_destroy(srv)
+        # --- one at a time (FIFO over the same trace)
+        stream = torch.cuda.current_stream()
+        plat = []
+        t0 = time.perf_counter()
+        for i, (at, gi, src) in enumerate(trace):
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            graphs[gi][1].solve(src, bufs[gi][i % nbuf], None, None, stream)
+            torch.cuda.synchronize()
+            plat.append((time.perf_counter() - t0 - at) * 1e3)
+        p_end = time.perf_counter() - t0
+        plat = np.array(plat)
+        out.append({"rate_qps": rate, "queries": count,
+                    "served": {"qps": round(count / t_end, 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                               "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                               "joined_running": sstats["joined_running"],
+                               "max_resident": sstats["max_resident"]},
+                    "plain_solve": {"qps": round(count / p_end, 1),
+                                    "p50_ms": round(float(np.percentile(plat, 50)), 3),
+                                    "p99_ms": round(float(np.percentile(plat, 99)), 3)}})
+    return {"graphs": list(SERVE_GRAPHS), "arrivals": "Poisson, seed 3; graph uniform, source uniform over "
+                                                       "the giant component", "results": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,6 +321,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving/cpu legs")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tune-ms", type=int, default=6000, help="autotune budget (0 = feature prior only)")
+    ap.add_argument("--serve-rates", default="100,1000", help="serving leg arrival rates (q/s)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival span per rate")
+    ap.add_argument("--serve-max", type=int, default=2000, help="queries per rate at most")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -316,6 +448,16 @@ def main():
         line["cpu_baseline"] = {"value": round(cg, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
                                 "sample": f"{cores} single-source Dijkstra runs on {args.workload}, "
                                           f"one per thread ({cdt:.1f} s)"}
+    if rank == 0 and not args.no_extras:
+        line["batch"] = [batch_leg(S, gg, torch, "u32"), batch_leg(S, gg, torch, "f32")]
+        cache = {}
+        if args.workload in SERVE_GRAPHS:
+            cache[args.workload] = (g, G, gg.giant_sources(g, 4096, seed=2)[0])
+        rates = [float(r) for r in args.serve_rates.split(",") if r]
+        line["serving"] = serve_leg(S, gg, torch, rates, args.serve_seconds, args.serve_max, cache)
+        for name, (_, Gc, _) in cache.items():
+            if Gc is not G:
+                Gc.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     G.close()

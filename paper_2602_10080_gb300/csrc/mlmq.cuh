@@ -58,6 +58,7 @@ constexpr int kFarCap = 64;         // per-warp far staging (elements)
 constexpr int kMaxClaim = 8;        // chunks per L2 claim (upper bound)
 constexpr int kStageCap = 64;       // block staging per L2 bucket (elements)
 constexpr uint32_t kInfU32 = 0xffffffffu;
+constexpr uint32_t kEmptyKey = 0xffffffffu;  // a free L1 slot (never a valid element key)
 constexpr uint32_t kSatU32 = 0xfffffffeu;
 constexpr uint32_t kInfF32 = 0x7f800000u;
 
@@ -76,6 +77,7 @@ enum : int {
     kStChunks, kStFlush, kStFar, kStCasFail, kStDeferred, kStRelaxShadow,
     // SM clock cycles spent per phase (lane 0 of every warp, summed)
     kCyRelax, kCyL1, kCyL2Write, kCyGlobalRead, kCyIdle, kCyL0,
+    kStLockSpin, kStWaitSpin, kStIdleIter, kStRefillTry, kStIter, kStRounds,
     kStCount
 };
 
@@ -241,6 +243,7 @@ template <> struct Arith<1> {
 
 struct BlockShared {
     int lock;                     // L1 lock (one warp at a time)
+    int slock;                    // far-write staging lock
     int refill;                   // one warp of the block refills L1 from L2
     uint32_t head, tail;          // L1 ring (V, FQ, SLF) or the near ring (NF)
     uint32_t fhead, ftail;        // NF far ring
@@ -372,31 +375,43 @@ struct Worker {
         __syncwarp();
     }
 
-    // ---- L1 lock -----------------------------------------------------------
-    __device__ bool lock() {
+    // ---- block locks ----------------------------------------------------------
+    // One warp at a time: the L1 ring (word = &S->lock) and the far-write
+    // staging (word = &S->slock) have separate locks.  Lane 0 spins on a
+    // plain read and only then tries the atomic (test-and-test-and-set),
+    // with a growing sleep, so waiters do not flood the shared-memory
+    // atomic unit while the holder works.
+    __device__ bool lock(int* word) {
         int ok = 1;
         mark(2);
         if (lane == 0) {
-            uint32_t spins = 0;
-            while (atomicCAS(&S->lock, 0, 1) != 0) {
-                if ((++spins & 1023u) == 0 && expired()) {
+            uint32_t spins = 0, ns = 16;
+            for (;;) {
+                if (*(volatile int*)word == 0 && atomicCAS(word, 0, 1) == 0) break;
+                if ((++spins & 255u) == 0 && expired()) {
                     raise_error(P.ctrl, kErrTimeout, 1, 0);
                     ok = 0;
                     break;
                 }
-                __nanosleep(20);
+                __nanosleep(ns);
+                ns = ns < 256u ? ns * 2u : 256u;
             }
+            sst[kStLockSpin] += spins;
         }
         ok = __shfl_sync(kFull, ok, 0);
         __threadfence_block();
         return ok != 0;
     }
-    __device__ void unlock() {
+    __device__ void unlock(int* word) {
         __threadfence_block();
         __syncwarp();
-        if (lane == 0) atomicExch(&S->lock, 0);
+        if (lane == 0) atomicExch(word, 0);
         __syncwarp();
     }
+    __device__ __forceinline__ bool lock() { return lock(&S->lock); }
+    __device__ __forceinline__ void unlock() { unlock(&S->lock); }
+    __device__ __forceinline__ bool slock() { return lock(&S->slock); }
+    __device__ __forceinline__ void sunlock() { unlock(&S->slock); }
 
     // ---- L2: sharded bucket rings -----------------------------------------
     __device__ __forceinline__ unsigned long long window() const {
@@ -475,6 +490,7 @@ struct Worker {
                     }
                     __nanosleep(32);
                 }
+                if (spins) atomicAdd(&sst[kStWaitSpin], (unsigned long long)spins);
             }
         }
         const int ldr = __ffs(grp) - 1;
@@ -603,6 +619,7 @@ struct Worker {
                 }
                 __nanosleep(32);
             }
+            if (spins) atomicAdd(&sst[kStWaitSpin], (unsigned long long)spins);
             if (ok) cnt = P.l2.cnt[slot];
         }
         okr = __all_sync(kFull, ok != 0);
@@ -764,6 +781,107 @@ struct Worker {
         stat(kStFlush, 1);
     }
 
+    // ---- L1 vector / filter policies: lock-free ring ------------------------
+    // Slots hold an element or kEmptyKey (64-bit stores, so a slot is seen
+    // whole).  Writers reserve slots by CAS on tail (bounded by head + cap),
+    // wait for each reserved slot to be empty (its reader of the previous
+    // lap has cleared it) and store; readers reserve up to 32 slots by CAS on
+    // head (bounded by tail), wait for each slot to be filled, take it and
+    // clear it.  Both waits are on warps that are already inside the same
+    // operation, so they are short; they are bounded by the deadline.
+    __device__ __forceinline__ bool l1_lockfree() const { return P.l1_type == 0 || P.l1_type == 2; }
+
+    template <int K>
+    __device__ void l1_write_lf(uint2 (&e)[K], bool (&valid)[K], int count_add, uint32_t fthr) {
+        const uint32_t cap = (uint32_t)P.l1_cap;
+        // the elements become visible to other warps: count them first
+        if (lane == 0 && count_add != 0)
+            atomicAdd(&S->acct, ((unsigned long long)(uint32_t)count_add) << 32);
+        __syncwarp();
+        bool out[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const bool want = valid[k] && (P.l1_type != 2 ||
+                                           (MQ && P.qoff ? abs_bucket(e[k].x, e[k].y) <= fthr : e[k].y <= fthr));
+            const uint32_t wm = __ballot_sync(kFull, want);
+            out[k] = valid[k] && !want;
+            if (!wm) continue;
+            const uint32_t c = __popc(wm);
+            uint32_t base = 0, take = 0;
+            if (lane == 0) {
+                uint32_t t = *(volatile uint32_t*)&S->tail;
+                for (;;) {
+                    const uint32_t h = *(volatile uint32_t*)&S->head;
+                    const uint32_t used = t - h;
+                    take = used < cap ? min(c, cap - used) : 0u;
+                    if (take == 0) break;
+                    const uint32_t old = atomicCAS(&S->tail, t, t + take);
+                    if (old == t) break;
+                    t = old;
+                }
+                base = t;
+            }
+            base = __shfl_sync(kFull, base, 0);
+            take = __shfl_sync(kFull, take, 0);
+            const uint32_t rank = __popc(wm & lanemask_lt());
+            const bool placed = want && rank < take;
+            out[k] = out[k] || (want && !placed);
+            int ok = 1;
+            if (placed) {
+                volatile uint2* slot = &L1[(base + rank) & l1_mask()];
+                uint32_t spins = 0;
+                while (vld(slot).x != kEmptyKey) {
+                    if ((++spins & 255u) == 0 && expired()) {
+                        raise_error(P.ctrl, kErrTimeout, 10, 0);
+                        ok = 0;
+                        break;
+                    }
+                }
+                if (ok) vst(slot, e[k]);
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) dec += l2_write(out[k], e[k]);
+    }
+
+    __device__ bool l1_read_lf(bool& valid, uint2& e) {
+        valid = false;
+        uint32_t h = 0, c = 0;
+        if (lane == 0) {
+            h = *(volatile uint32_t*)&S->head;
+            for (;;) {
+                const uint32_t t = *(volatile uint32_t*)&S->tail;
+                c = t - h < 32u ? t - h : 32u;
+                if (c == 0) break;
+                const uint32_t old = atomicCAS(&S->head, h, h + c);
+                if (old == h) break;
+                h = old;
+            }
+        }
+        c = __shfl_sync(kFull, c, 0);
+        if (c == 0) return false;
+        h = __shfl_sync(kFull, h, 0);
+        if (lane < c) {
+            volatile uint2* slot = &L1[(h + lane) & l1_mask()];
+            uint32_t spins = 0;
+            uint2 x = vld(slot);
+            while (x.x == kEmptyKey) {
+                if ((++spins & 255u) == 0 && expired()) {
+                    raise_error(P.ctrl, kErrTimeout, 11, 0);
+                    break;
+                }
+                x = vld(slot);
+            }
+            valid = x.x != kEmptyKey;
+            e = x;
+            vst(slot, make_uint2(kEmptyKey, 0u));
+        }
+        __syncwarp();
+        stat(kStPopL1, 1);
+        return true;
+    }
+
     // Write primitive of the L1 level for K elements per lane; `count_add`
     // of them are not yet in the block count (see l1_place).  `filter`
     // applies the L1FQ threshold.
@@ -777,6 +895,24 @@ struct Worker {
             win = __shfl_sync(kFull, win, 0);
             fthr = MQ && P.qoff ? (uint32_t)win + (uint32_t)P.filter_deltas       // bucket W + F
                                 : A::upper((uint32_t)win, P.delta, P.filter_deltas);  // (W + F) * delta
+        }
+        if (l1_lockfree()) {
+            l1_write_lf<K>(e, valid, count_add, fthr);
+            if (P.wb > 0) {
+                // L1V periodic flush (Section 3.4): every wb-th write moves L1 to L2
+                uint32_t wc = 0;
+                if (lane == 0) wc = atomicAdd(&S->writes, 1u) + 1u;
+                wc = __shfl_sync(kFull, wc, 0);
+                if (wc % (uint32_t)P.wb == 0u) {
+                    bool v = false;
+                    uint2 x = make_uint2(0, 0);
+                    for (uint32_t n = 0; n <= (uint32_t)P.l1_cap / 32u && l1_read_lf(v, x); n++)
+                        dec += l2_write(v, x);
+                    stat(kStFlush, 1);
+                }
+            }
+            stat(kCyL1, (unsigned long long)((unsigned long long)(clock64() - c0)));
+            return;
         }
         bool out[K];
         if (!lock()) return;
@@ -808,6 +944,7 @@ struct Worker {
             if (P.l1_type == 1) any |= *(volatile uint32_t*)&S->fhead != *(volatile uint32_t*)&S->ftail;
         }
         if (!__shfl_sync(kFull, any, 0)) return false;
+        if (l1_lockfree()) return l1_read_lf(valid, e);
         if (!lock()) return false;
         const uint32_t cap = (uint32_t)P.l1_cap;
         uint32_t h = sread(&S->head), t = sread(&S->tail);
@@ -886,6 +1023,7 @@ struct Worker {
         }
         role = __shfl_sync(kFull, role, 0);
         if (!role) return -1;
+        stat(kStRefillTry, 1);
         stage_flush(false);
         uint32_t want = (uint32_t)P.claim;
         const uint32_t room = l1_free() / kChunk;
@@ -1042,9 +1180,9 @@ struct Worker {
             const uint32_t bf = (uint32_t)(__ffs(m) - 1);
             bool v = false;
             uint2 x = make_uint2(0, 0);
-            if (!lock()) return;
+            if (!slock()) return;
             stage_take(bf, v, x);
-            unlock();
+            sunlock();
             dec += l2_write(v, x);
         }
     }
@@ -1073,7 +1211,7 @@ struct Worker {
             if (!__any_sync(kFull, sv)) continue;
             bool vy = false, over = false;
             uint2 y = make_uint2(0, 0);
-            if (!lock()) return;
+            if (!slock()) return;
             // the staged elements become visible to the block: count every
             // private push now (counting early only delays the done flush)
             if (lane == 0 && unc != 0) atomicAdd(&S->acct, ((unsigned long long)(uint32_t)unc) << 32);
@@ -1095,7 +1233,7 @@ struct Worker {
                 const uint32_t bf = __shfl_sync(kFull, b, __ffs(fm) - 1);
                 stage_take(bf, vy, y);
             }
-            unlock();
+            sunlock();
             dec += l2_write(vy, y);
             dec += l2_write(over, x);
         }
@@ -1147,6 +1285,37 @@ struct Worker {
         }
     }
 
+    // relax() with dist[v] already loaded (cur).  Without predecessors, and
+    // with the packed (dist, pred) minimum, the update is a reduction whose
+    // old value is not waited for: the element is pushed when nd beat the
+    // loaded value.  Every write that lowers dist[v] saw a larger value
+    // when it loaded, so the final value is always pushed; a push that
+    // lost the race carries a larger distance and is dropped as stale.
+    __device__ __forceinline__ bool relax_cur(size_t vidx, uint32_t u, uint32_t du, uint32_t wbits, DistT cur,
+                                              uint32_t& nd) {
+        nd = A::add(du, wbits);
+        if (PRED == 0) {
+            if (nd >= (uint32_t)cur) return false;
+            atomicMin(reinterpret_cast<uint32_t*>(dist) + vidx, nd);
+            return true;
+        } else if (PRED == 1) {
+            const unsigned long long cand = ((unsigned long long)nd << 32) | u;
+            if (cand >= (unsigned long long)cur) return false;
+            atomicMin(reinterpret_cast<unsigned long long*>(dist) + vidx, cand);
+            return (uint32_t)((unsigned long long)cur >> 32) > nd;
+        } else {
+            unsigned long long* p = reinterpret_cast<unsigned long long*>(dist) + vidx;
+            const unsigned long long cand = ((unsigned long long)nd << 32) | u;
+            unsigned long long c = (unsigned long long)cur;
+            while ((uint32_t)(c >> 32) > nd) {
+                const unsigned long long old = atomicCAS(p, c, cand);
+                if (old == c) return true;
+                c = old;
+            }
+            return false;
+        }
+    }
+
     // route the improved elements of one round: writes through light arcs
     // (w <= near_w, the light/heavy split of delta-stepping) go to L0, the
     // others to the far staging and then their L2 bucket
@@ -1162,6 +1331,36 @@ struct Worker {
         }
         far_push(imp && !nearv, make_uint2(key, nd));
         stat(kStImproved, (unsigned long long)(__popc(__ballot_sync(kFull, imp))));
+    }
+
+    // One lane's arc of a relaxation round: the adjacency entry (col,
+    // weight bits) and its source's distance, query and predecessor id.
+    struct RoundIn {
+        uint2 a;
+        uint32_t du, q, pu;
+        bool in;
+    };
+
+    // Arc g = g0 + lane of the batch's concatenated adjacency: its owner
+    // is the largest lane j with ex[j] <= g; issues the adjacency load.
+    __device__ __forceinline__ RoundIn round_in(int32_t g0, int32_t total, int32_t ex, int32_t rs, uint32_t du,
+                                                uint32_t myq, uint32_t pu) const {
+        RoundIn r;
+        const int32_t g = g0 + (int32_t)lane;
+        int j = 0;
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            int32_t t = __shfl_sync(kFull, ex, j + s);
+            if (t <= g) j += s;
+        }
+        const int32_t oex = __shfl_sync(kFull, ex, j);
+        const int32_t ors = __shfl_sync(kFull, rs, j);
+        r.du = __shfl_sync(kFull, du, j);
+        r.q = MQ ? __shfl_sync(kFull, myq, j) : 0u;
+        r.pu = PRED != 0 ? __shfl_sync(kFull, pu, j) : 0u;
+        r.in = g < total;
+        r.a = r.in ? __ldg(P.adj + (ors + (g - oex))) : make_uint2(0u, 0u);
+        return r;
     }
 
     // Relaxes a batch of up to 32 vertices (one per lane).  Stale elements are
@@ -1236,39 +1435,25 @@ struct Worker {
             if (shs) stat(kStRelaxShadow, (unsigned long long)shs);
         }
         for (int32_t g0 = 0; g0 < total; g0 += 32) {
-            if ((g0 & 4095) == 4064) {
+            if (g0 && (g0 & 4095) == 0) {
                 int stop = 0;
                 if (lane == 0) stop = expired() || ld_volatile_int(&P.ctrl->error) != 0;
                 if (__shfl_sync(kFull, stop, 0)) break;
             }
-            const int32_t g = g0 + (int32_t)lane;
-            // owner: the largest lane j with ex[j] <= g
-            int j = 0;
-#pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                int32_t t = __shfl_sync(kFull, ex, j + s);
-                if (t <= g) j += s;
-            }
-            const int32_t oex = __shfl_sync(kFull, ex, j);
-            const int32_t ors = __shfl_sync(kFull, rs, j);
-            const uint32_t odu = __shfl_sync(kFull, du, j);
-            const uint32_t oq = __shfl_sync(kFull, myq, j);
-            const uint32_t opu = PRED != 0 ? __shfl_sync(kFull, pu, j) : 0u;
+            stat(kStRounds, 1);
+            const RoundIn cu = round_in(g0, total, ex, rs, du, myq, pu);
+            uint32_t nd = 0;
             bool imp = false;
-            uint32_t nd = 0, v = 0, w = 0;
-            if (g < total) {
-                uint2 a = __ldg(P.adj + (ors + (g - oex)));
-                v = a.x;
-                w = a.y;
-                size_t vidx = MQ ? (size_t)oq * (size_t)P.nv + v : (size_t)v;
-                imp = relax(vidx, opu, odu, w, nd);
+            if (cu.in) {
+                const size_t vidx = MQ ? (size_t)cu.q * (size_t)P.nv + cu.a.x : (size_t)cu.a.x;
+                imp = relax_cur(vidx, cu.pu, cu.du, cu.a.y, ld_dist(dist + vidx), nd);
             }
-            push_round(imp, MQ ? ((oq << P.vbits) | v) : v, nd, w);
+            push_round(imp, MQ ? ((cu.q << P.vbits) | cu.a.x) : cu.a.x, nd, cu.a.y);
         }
         return consumed;
     }
 
-    __device__ void publish_stats() {
+    __device__ __noinline__ void publish_stats() {
         if (lane == 0) {
             for (int i = 0; i < kStCount; i++)
                 if (sst[i]) atomicAdd(&P.ctrl->stats[i], sst[i]);
@@ -1281,6 +1466,7 @@ struct Worker {
         uint32_t iter = 0;
         for (;;) {
             mark(1, iter);
+            stat(kStIter, 1);
             if ((++iter & 7u) == 0 || idle_ns) {
                 int stop = 0;
                 if (lane == 0) {
@@ -1335,6 +1521,7 @@ struct Worker {
                 }
                 fin = __shfl_sync(kFull, fin, 0);
                 if (fin) break;
+                stat(kStIdleIter, 1);
                 idle_ns = idle_ns ? min(idle_ns * 2u, 1024u) : 64u;
                 __nanosleep(idle_ns);
                 stat(kCyIdle, (unsigned long long)((unsigned long long)(clock64() - c3)));
@@ -1356,7 +1543,7 @@ struct Worker {
     // L2.  After a normal termination there is nothing left and this is a
     // no-op; at the end of a serving slice the work continues from L2 in the
     // next launch.
-    __device__ void drain_warp() {
+    __device__ __noinline__ void drain_warp() {
         if (ld_volatile_int(&P.ctrl->error) != 0) return;
         const uint32_t len = l0t - l0h;
         if (len) {
@@ -1374,9 +1561,13 @@ struct Worker {
 
     // End of a launch, one warp per block after every warp drained: move L1
     // and the block staging to L2, then publish the block's count.
-    __device__ void drain_block() {
+    __device__ __noinline__ void drain_block() {
         if (ld_volatile_int(&P.ctrl->error) != 0) return;
-        if (lock()) {
+        if (l1_lockfree()) {
+            bool v = false;
+            uint2 x = make_uint2(0, 0);
+            while (l1_read_lf(v, x)) dec += l2_write(v, x);
+        } else if (lock()) {
             if (P.l1_type == 1) {
                 const uint32_t half = (uint32_t)P.l1_cap >> 1;
                 for (int rg = 0; rg < 2; rg++) {
@@ -1433,6 +1624,7 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
     uint2* stage = reinterpret_cast<uint2*>(smem + P.stage_off);
     if (threadIdx.x == 0) {
         S->lock = 0;
+        S->slock = 0;
         S->refill = 0;
         S->head = S->tail = S->fhead = S->ftail = 0;
         S->writes = 0;
@@ -1448,6 +1640,7 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
             S->slice_end = prev ? prev : mine;
         }
     }
+    for (int i = threadIdx.x; i < P.l1_cap; i += blockDim.x) vst(l1 + i, make_uint2(kEmptyKey, 0u));
     __syncthreads();
     const unsigned long long deadline = gtime() + P.timeout_ns;
     const int warp = threadIdx.x >> 5;

@@ -536,7 +536,7 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
     const bool mq = nq > 1;
     int vbits = 0;
     if (mq) {
-        while (vbits < 31 && (1ll << vbits) < (long long)nv) vbits++;
+        while (vbits < 31 && (1ll << vbits) <= (long long)nv) vbits++;  // 2^vbits > nv: no key is all ones
         if (vbits == 0) vbits = 1;
         if ((unsigned long long)nq << vbits > (1ull << 32)) return SSSP_E_INVAL;
     }
@@ -721,6 +721,13 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
                          (long long)st.refills, (long long)st.relax_arcs, (long long)st.improved,
                          (long long)st.far_pushes, (long long)st.stale, (long long)st.l2_chunks_written,
                          (long long)st.cas_fail, hc.error, hc.finished);
+        if (dbg > 1)
+            std::fprintf(stderr, "[sssp]   iter %llu rounds %llu idle %llu refill_try %llu refills %llu lock_spin %llu "
+                                 "wait_spin %llu cycles relax/l1/l2w/gread/idle/l0 %llu/%llu/%llu/%llu/%llu/%llu\n",
+                         hc.stats[kStIter], hc.stats[kStRounds], hc.stats[kStIdleIter], hc.stats[kStRefillTry],
+                         hc.stats[kStRefill], hc.stats[kStLockSpin], hc.stats[kStWaitSpin], hc.stats[kCyRelax],
+                         hc.stats[kCyL1], hc.stats[kCyL2Write], hc.stats[kCyGlobalRead], hc.stats[kCyIdle],
+                         hc.stats[kCyL0]);
         if (hc.error == kErrNone && hc.finished) return SSSP_OK;
         if (dbg)
             std::fprintf(stderr, "[sssp] solve failed: error=%d where=%d info=%d finished=%d reserve=%llu done=%llu "

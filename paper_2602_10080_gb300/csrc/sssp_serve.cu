@@ -506,7 +506,7 @@ Lane* lane_create(sssp_server* s, Graph* g, int pred_mode, int* rc) {
         delete L;
         return nullptr;
     }
-    while (L->vbits < 31 && (1ll << L->vbits) < (long long)g->nv) L->vbits++;
+    while (L->vbits < 31 && (1ll << L->vbits) <= (long long)g->nv) L->vbits++;  // 2^vbits > nv
     L->cap_limit = (uint32_t)std::min<uint64_t>((uint64_t)s->opt.max_slots, 1ull << (32 - L->vbits));
     L->cell = pred_mode ? 8 : 4;
     L->idle_since = Clock::now();
