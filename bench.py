@@ -256,7 +256,7 @@ def serve_leg(S, gg, torch, rates, seconds: float, max_queries: int, graph_cache
             srcs = graphs[gi][2]
             trace.append((float(arr[i]), gi, int(srcs[min(int(us[i] * len(srcs)), len(srcs) - 1)])))
         # --- served
-        srv = S.sssp_serve_create(slice_us=500)
+        srv = S.sssp_serve_create(slice_us=1000)
         try:
             # warm the lanes (allocation, first launch) outside the trace
             warm = [S.sssp_serve_submit(srv, G.handle, int(srcs[0]), bufs[gi][0], None)

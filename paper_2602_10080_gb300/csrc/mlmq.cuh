@@ -1467,7 +1467,7 @@ struct Worker {
         for (;;) {
             mark(1, iter);
             stat(kStIter, 1);
-            if ((++iter & 7u) == 0 || idle_ns) {
+            if ((++iter & 7u) == 0 || idle_ns || P.slice_ns) {
                 int stop = 0;
                 if (lane == 0) {
                     stop = aborted();

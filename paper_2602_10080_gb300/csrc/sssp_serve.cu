@@ -25,6 +25,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -117,23 +118,70 @@ __global__ void serve_seed_kernel(KParams P, const int2* adm, int32_t nadm, uint
 
 // Counts the L2 elements of every slot (live[slot]) and the fullest ring's
 // chunk count (occ[0]).  Runs between slices, when every chunk in [rt, wt)
-// of a ring is full.  Block b scans ring b / 4, warps stride over chunks.
+// of a ring is full.  Every block prefix-sums the rings' chunk counts in
+// shared memory; the warps of the grid then take the concatenated chunks
+// in turn, so one very full ring does not serialise the scan.
+constexpr int kScanMaxRings = 1024;
 __global__ void serve_scan_kernel(Rings R, uint32_t nrings, int32_t vbits, uint32_t cap, uint32_t* live,
                                   uint32_t* occ) {
-    const uint32_t ring = blockIdx.x >> 2, part = blockIdx.x & 3u;
-    if (ring >= nrings) return;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t r = R.rt[(size_t)ring * 32], w = R.wt[(size_t)ring * 32];
-    const uint32_t count = w - r;
-    if (threadIdx.x == 0 && part == 0) atomicMax(occ, count);
-    for (uint32_t j = part * nw + warp; j < count; j += 4u * nw) {
-        const size_t slot = (size_t)ring * R.nch + ((r + j) & (R.nch - 1u));
-        const uint32_t c = R.cnt[slot];
-        const bool v = lane < c;
-        const uint32_t q = v ? (R.data[slot * kChunk + lane].x >> vbits) : 0xffffffffu;
-        const uint32_t grp = __match_any_sync(kFull, q);
-        if (v && q < cap && (grp & lanemask_lt()) == 0u) atomicAdd(live + q, (uint32_t)__popc(grp));
+    __shared__ uint32_t pre[kScanMaxRings + 1];
+    __shared__ uint32_t rbase[kScanMaxRings];
+    for (uint32_t k = threadIdx.x; k < nrings; k += blockDim.x) {
+        const uint32_t r = R.rt[(size_t)k * 32], w = R.wt[(size_t)k * 32];
+        rbase[k] = r;
+        pre[k] = w - r;
+        if (blockIdx.x == 0 && w != r) atomicMax(occ, w - r);
     }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // exclusive prefix sum: lane i owns a contiguous segment of the rings
+        const uint32_t l = threadIdx.x, per = (nrings + 31u) / 32u;
+        const uint32_t b = min(l * per, nrings), e = min(b + per, nrings);
+        uint32_t sum = 0;
+        for (uint32_t k = b; k < e; k++) sum += pre[k];
+        uint32_t incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(kFull, incl, o);
+            if (l >= (uint32_t)o) incl += x;
+        }
+        uint32_t acc = incl - sum;
+        for (uint32_t k = b; k < e; k++) {
+            const uint32_t c = pre[k];
+            pre[k] = acc;
+            acc += c;
+        }
+        if (l == 31) {
+            pre[nrings] = incl;
+            if (blockIdx.x == 0) occ[1] = incl;
+        }
+    }
+    __syncthreads();
+    const uint32_t total = pre[nrings];
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    // per-block counts in shared memory, one global add per slot at the end
+    extern __shared__ uint32_t hist[];
+    for (uint32_t k = threadIdx.x; k < cap; k += blockDim.x) hist[k] = 0;
+    __syncthreads();
+    for (uint32_t c = gw; c < total; c += nwarps) {
+        // ring: the last k with pre[k] <= c
+        uint32_t lo = 0, hi = nrings;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (pre[mid] <= c) lo = mid;
+            else hi = mid;
+        }
+        const size_t slot = (size_t)lo * R.nch + ((rbase[lo] + (c - pre[lo])) & (R.nch - 1u));
+        const uint32_t n = R.cnt[slot];
+        if (lane < n) {
+            const uint32_t q = R.data[slot * kChunk + lane].x >> vbits;
+            if (q < cap) atomicAdd(hist + q, 1u);
+        }
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < cap; k += blockDim.x)
+        if (hist[k]) atomicAdd(live + k, hist[k]);
 }
 
 // Copies every ring's live chunks [rt, wt) to the front of the matching
@@ -253,7 +301,7 @@ struct Lane {
     Ctrl* ctrl = nullptr;
     Ctrl* ctrl_h = nullptr;
     cudaStream_t stream = nullptr;
-    cudaEvent_t k0 = nullptr, k1 = nullptr;
+    cudaEvent_t k0 = nullptr, k1 = nullptr, k2 = nullptr;
     size_t bytes = 0;           // device bytes charged to the budget
     std::vector<Query*> slot_q; // [cap]: query in the slot (nullptr = free or draining)
     std::vector<uint8_t> drain; // [cap]: slot holds a cancelled query's leftover elements
@@ -263,7 +311,11 @@ struct Lane {
     bool injected = false;      // a test flag's injected failure has been applied
     int draining = 0;
     int nadm = 0;               // admissions staged for the next slice
-    bool launched = false;
+    bool inflight = false;      // a slice is queued or running on the stream
+    cudaEvent_t done_ev = nullptr;
+    Clock::time_point t_launch;
+    double dbg_wall_ms = 0, dbg_kernel_ms = 0, dbg_host_ms = 0, dbg_scan_ms = 0, dbg_chunks = 0, dbg_elems = 0;
+    int dbg_slices = 0;
     Clock::time_point idle_since;
 };
 
@@ -284,6 +336,7 @@ struct sssp_server {
     uint64_t next_ticket = 1;
     bool stop = false;
     int fatal = SSSP_OK;        // sticky CUDA failure
+    int debug = 0;              // SSSP_DEBUG level
     sssp_serve_stats stats{};
     std::thread worker;
     // worker-thread state
@@ -328,6 +381,8 @@ void lane_destroy(sssp_server* s, Lane* L) {
     lane_free_buffers(s, L);
     if (L->k0) cudaEventDestroy(L->k0);
     if (L->k1) cudaEventDestroy(L->k1);
+    if (L->k2) cudaEventDestroy(L->k2);
+    if (L->done_ev) cudaEventDestroy(L->done_ev);
     if (L->stream) cudaStreamDestroy(L->stream);
     delete L;
 }
@@ -430,13 +485,13 @@ int lane_grow_slots(sssp_server* s, Lane* L, uint32_t want) {
     if (ncap <= L->cap) return SSSP_E_BUSY;
     const size_t nv = (size_t)L->g->nv;
     const size_t work_b = (size_t)ncap * nv * L->cell;
-    const size_t side_b = (size_t)ncap * (4 + 8) + (size_t)(ncap + 1) * 4;
-    const size_t old_b = (size_t)L->cap * nv * L->cell + (size_t)L->cap * (4 + 8) + (size_t)(L->cap + 1) * 4;
+    const size_t side_b = (size_t)ncap * (4 + 8) + (size_t)(ncap + 2) * 4;
+    const size_t old_b = L->cap ? (size_t)L->cap * nv * L->cell + (size_t)L->cap * (4 + 8) + (size_t)(L->cap + 2) * 4 : 0;
     if (s->used - old_b + work_b + side_b > s->budget) return SSSP_E_NOMEM;
     void* work = nullptr;
     uint32_t *qoff = nullptr, *live = nullptr;
     int2* adm = nullptr;
-    if (dev_alloc((char**)&work, work_b) || dev_alloc(&qoff, ncap) || dev_alloc(&live, (size_t)ncap + 1) ||
+    if (dev_alloc((char**)&work, work_b) || dev_alloc(&qoff, ncap) || dev_alloc(&live, (size_t)ncap + 2) ||
         dev_alloc(&adm, ncap)) {
         cudaFree(work);
         cudaFree(qoff);
@@ -446,7 +501,7 @@ int lane_grow_slots(sssp_server* s, Lane* L, uint32_t want) {
     }
     uint32_t* live_h = nullptr;
     int2* adm_h = nullptr;
-    if (cudaMallocHost((void**)&live_h, ((size_t)ncap + 1) * 4) != cudaSuccess ||
+    if (cudaMallocHost((void**)&live_h, ((size_t)ncap + 2) * 4) != cudaSuccess ||
         cudaMallocHost((void**)&adm_h, (size_t)ncap * sizeof(int2)) != cudaSuccess) {
         cudaGetLastError();
         if (live_h) cudaFreeHost(live_h);
@@ -512,6 +567,8 @@ Lane* lane_create(sssp_server* s, Graph* g, int pred_mode, int* rc) {
     L->idle_since = Clock::now();
     if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&L->k0) != cudaSuccess || cudaEventCreate(&L->k1) != cudaSuccess ||
+        cudaEventCreate(&L->k2) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L->done_ev, cudaEventDisableTiming) != cudaSuccess ||
         dev_alloc(&L->ctrl, 1) || cudaMallocHost((void**)&L->ctrl_h, sizeof(Ctrl)) != cudaSuccess) {
         cudaGetLastError();
         *rc = SSSP_E_NOMEM;
@@ -598,7 +655,7 @@ void admit(sssp_server* s) {
         }
         const int pm = q->pred_out ? pred_mode_for(q->g) : 0;
         Lane* L = find_lane(s, q->g, pm);
-        if (L && std::find(blocked.begin(), blocked.end(), L) != blocked.end()) {
+        if (L && (L->inflight || std::find(blocked.begin(), blocked.end(), L) != blocked.end())) {
             keep.push_back(q);
             continue;
         }
@@ -614,7 +671,7 @@ void admit(sssp_server* s) {
                 // free idle lanes and try once more
                 for (size_t i = 0; i < s->lanes.size();) {
                     Lane* o = s->lanes[i];
-                    if (o != L && o->running == 0 && o->draining == 0 && o->nadm == 0) {
+                    if (o != L && !o->inflight && o->running == 0 && o->draining == 0 && o->nadm == 0) {
                         lane_destroy(s, o);
                         s->lanes.erase(s->lanes.begin() + (long)i);
                     } else {
@@ -665,15 +722,13 @@ void admit(sssp_server* s) {
     for (auto it = keep.rbegin(); it != keep.rend(); ++it) s->backlog.push_front(*it);
 }
 
-// Launches one slice on every lane with work.  Returns the lanes launched.
-int launch_slices(sssp_server* s, std::vector<Lane*>& launched) {
-    launched.clear();
+// Launches one slice on every lane that has work and no slice in flight.
+int launch_ready(sssp_server* s) {
     int nact = 0;
     for (Lane* L : s->lanes)
         if (L->running + L->draining > 0) nact++;
     for (Lane* L : s->lanes) {
-        L->launched = false;
-        if (L->running + L->draining == 0) continue;
+        if (L->inflight || L->running + L->draining == 0) continue;
         KParams P = L->plan.P;
         P.nq = (int32_t)L->cap;
         P.dist = L->work;
@@ -683,6 +738,8 @@ int launch_slices(sssp_server* s, std::vector<Lane*>& launched) {
         P.ctrl = L->ctrl;
         P.slice_ns = (unsigned long long)s->opt.slice_us * 1000ull;
         P.qoff = L->qoff;
+        // a warp's batch stays short, so a slice ends close to its deadline
+        P.max_arcs = std::min(P.max_arcs, 1024);
         const bool packed = L->pred_mode != 0;
         if (L->nadm) {
             cudaMemcpyAsync(L->adm, L->adm_h, (size_t)L->nadm * sizeof(int2), cudaMemcpyHostToDevice, L->stream);
@@ -697,15 +754,17 @@ int launch_slices(sssp_server* s, std::vector<Lane*>& launched) {
         cudaError_t e = launch_mlmq(L->plan.key, dim3(grid), dim3(L->plan.threads), L->plan.smem, L->stream, P);
         if (e != cudaSuccess) return cuda_status(e);
         cudaEventRecord(L->k1, L->stream);
-        cudaMemsetAsync(L->live, 0, ((size_t)L->cap + 1) * 4, L->stream);
-        serve_scan_kernel<<<L->nrings * 4, 256, 0, L->stream>>>(L->rings, L->nrings, L->vbits, L->cap,
-                                                               L->live, L->live + L->cap);
-        cudaMemcpyAsync(L->live_h, L->live, ((size_t)L->cap + 1) * 4, cudaMemcpyDeviceToHost, L->stream);
+        cudaMemsetAsync(L->live, 0, ((size_t)L->cap + 2) * 4, L->stream);
+        serve_scan_kernel<<<s->sms * 4, 256, (size_t)L->cap * 4, L->stream>>>(L->rings, L->nrings, L->vbits,
+                                                                             L->cap, L->live, L->live + L->cap);
+        cudaMemcpyAsync(L->live_h, L->live, ((size_t)L->cap + 2) * 4, cudaMemcpyDeviceToHost, L->stream);
+        cudaEventRecord(L->k2, L->stream);
         cudaMemcpyAsync(L->ctrl_h, L->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, L->stream);
+        cudaEventRecord(L->done_ev, L->stream);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
-        L->launched = true;
-        launched.push_back(L);
+        L->inflight = true;
+        L->t_launch = Clock::now();
         std::lock_guard<std::mutex> lk(s->mu);
         s->stats.slices++;
     }
@@ -740,32 +799,44 @@ void fail_all(sssp_server* s, int status) {
     for (Lane* L : s->lanes) {
         for (uint32_t k = 0; k < L->cap; k++)
             if (L->slot_q[k]) {
-                finish_query(s, L->slot_q[k], status);
+                if (!L->slot_q[k]->cancel) finish_query(s, L->slot_q[k], status);
                 L->slot_q[k] = nullptr;
             }
         L->running = 0;
         L->draining = 0;
     }
-    for (Query* q : s->backlog) finish_query(s, q, status);
+    for (Query* q : s->backlog)
+        if (!q->cancel) finish_query(s, q, status);
     s->backlog.clear();
-    for (Query* q : s->pending) finish_query(s, q, status);
+    for (Query* q : s->pending)
+        if (!q->cancel) finish_query(s, q, status);
     s->pending.clear();
     s->cv_done.notify_all();
 }
 
-// After the slices: completions, errors, ring growth.
-int collect(sssp_server* s, std::vector<Lane*>& launched) {
-    for (Lane* L : launched) {
+// After a lane's slice: completions, errors, ring growth.
+int collect_lane(sssp_server* s, Lane* L) {
+    L->inflight = false;
+    {
         cudaError_t e = cudaStreamSynchronize(L->stream);
         if (e != cudaSuccess) return cuda_status(e);
         float ms = 0;
         if (cudaEventElapsedTime(&ms, L->k0, L->k1) == cudaSuccess) {
             std::lock_guard<std::mutex> lk(s->mu);
             s->stats.kernel_ms += ms;
+            L->dbg_kernel_ms += ms;
+        }
+        if (s->debug > 1) {
+            float sm = 0;
+            if (cudaEventElapsedTime(&sm, L->k1, L->k2) == cudaSuccess) L->dbg_scan_ms += sm;
+            L->dbg_chunks += L->live_h[L->cap + 1];
+            for (uint32_t k = 0; k < L->cap; k++) L->dbg_elems += L->live_h[k];
         }
     }
     const Clock::time_point now = Clock::now();
-    for (Lane* L : launched) {
+    L->dbg_wall_ms += std::chrono::duration<double, std::milli>(now - L->t_launch).count();
+    L->dbg_slices++;
+    {
         Ctrl& hc = *L->ctrl_h;
         if (!L->injected && (s->opt.flags & (SSSP_SERVE_INJECT_OVERFLOW | SSSP_SERVE_INJECT_TIMEOUT))) {
             L->injected = true;
@@ -790,13 +861,13 @@ int collect(sssp_server* s, std::vector<Lane*>& launched) {
                     s->backlog.swap(keep);
                     s->cv_done.notify_all();
                 }
-                continue;
+                return SSSP_OK;
             }
             // a bounded wait ran out: the lane's queries fail, the lane starts over
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 for (uint32_t k = 0; k < L->cap; k++) {
-                    if (L->slot_q[k]) finish_query(s, L->slot_q[k], SSSP_E_TIMEOUT);
+                    if (L->slot_q[k] && !L->slot_q[k]->cancel) finish_query(s, L->slot_q[k], SSSP_E_TIMEOUT);
                     L->slot_q[k] = nullptr;
                     L->drain[k] = 0;
                 }
@@ -807,7 +878,7 @@ int collect(sssp_server* s, std::vector<Lane*>& launched) {
             L->running = L->draining = 0;
             int rc = lane_rings_fresh(s, L, L->rings.nch);
             if (rc == SSSP_E_CUDA) return rc;
-            continue;
+            return SSSP_OK;
         }
         // completions
         std::vector<std::pair<uint32_t, Query*>> done;
@@ -876,7 +947,7 @@ int collect(sssp_server* s, std::vector<Lane*>& launched) {
         // keep the free-slot stack ordered (lowest slot reused first)
         std::sort(L->free_slots.begin(), L->free_slots.end(), std::greater<uint32_t>());
         // rings more than half full: move to rings twice as large
-        const uint32_t occ = L->live_h[L->cap];
+        const uint32_t occ = L->live_h[L->cap];   // fullest ring (chunks); [cap + 1] = all rings
         const bool every = (s->opt.flags & SSSP_SERVE_MIGRATE_EACH_SLICE) != 0;
         if (L->running + L->draining > 0 && (every || (uint64_t)occ + lane_margin(L) > L->rings.nch / 2)) {
             const uint32_t nch = (uint64_t)occ + lane_margin(L) > L->rings.nch / 2 ? L->rings.nch * 2u : L->rings.nch;
@@ -892,26 +963,36 @@ int collect(sssp_server* s, std::vector<Lane*>& launched) {
             L->idle_since = Clock::now();
         }
     }
+    L->dbg_host_ms += std::chrono::duration<double, std::milli>(Clock::now() - now).count();
+    if (s->debug > 1 && L->dbg_slices == 100) {
+        std::fprintf(stderr, "[sssp serve] lane n=%d pred=%d cap=%u: 100 slices, kernel %.3f ms, scan %.3f ms, "
+                             "launch-to-seen %.3f ms, collect %.3f ms per slice; live chunks %.0f elements %.0f; "
+                             "running %d draining %d nch %u\n",
+                     L->g->n, L->pred_mode, L->cap, L->dbg_kernel_ms / 100, L->dbg_scan_ms / 100,
+                     L->dbg_wall_ms / 100, L->dbg_host_ms / 100, L->dbg_chunks / 100, L->dbg_elems / 100, L->running,
+                     L->draining, L->rings.nch);
+        L->dbg_slices = 0;
+        L->dbg_kernel_ms = L->dbg_wall_ms = L->dbg_host_ms = L->dbg_scan_ms = L->dbg_chunks = L->dbg_elems = 0;
+    }
     return SSSP_OK;
 }
 
 void worker_main(sssp_server* s) {
     cudaSetDevice(s->device);
-    std::vector<Lane*> launched;
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(s->mu);
             for (;;) {
                 bool busy = !s->pending.empty() || !s->backlog.empty();
                 for (Lane* L : s->lanes)
-                    if (L->running + L->draining > 0) busy = true;
+                    if (L->inflight || L->running + L->draining > 0) busy = true;
                 if (busy || s->stop) break;
                 s->cv_work.wait_for(lk, std::chrono::milliseconds(200));
                 // lanes idle for a while give their memory back
                 const Clock::time_point now = Clock::now();
                 for (size_t i = 0; i < s->lanes.size();) {
                     Lane* L = s->lanes[i];
-                    if (L->running + L->draining + L->nadm == 0 &&
+                    if (!L->inflight && L->running + L->draining + L->nadm == 0 &&
                         std::chrono::duration<double>(now - L->idle_since).count() > 5.0) {
                         lk.unlock();
                         lane_destroy(s, L);
@@ -924,7 +1005,7 @@ void worker_main(sssp_server* s) {
             }
             bool busy = !s->pending.empty() || !s->backlog.empty();
             for (Lane* L : s->lanes)
-                if (L->running + L->draining > 0) busy = true;
+                if (L->inflight || L->running + L->draining > 0) busy = true;
             if (s->stop && !busy) break;
             if (s->fatal) {
                 for (Query* q : s->pending) finish_query(s, q, s->fatal);
@@ -940,8 +1021,35 @@ void worker_main(sssp_server* s) {
             std::lock_guard<std::mutex> lk(s->mu);
             s->stats.max_resident = std::max<int64_t>(s->stats.max_resident, resident);
         }
-        int rc = launch_slices(s, launched);
-        if (!rc) rc = collect(s, launched);
+        int rc = launch_ready(s);
+        // wait for any lane's slice (lanes run on their own streams); come
+        // back now and then for new submissions to idle lanes
+        const Clock::time_point t0 = Clock::now();
+        bool any = false, inflight = false;
+        while (!rc) {
+            inflight = false;
+            for (Lane* L : s->lanes) {
+                if (!L->inflight) continue;
+                cudaError_t q = cudaEventQuery(L->done_ev);
+                if (q == cudaErrorNotReady) {
+                    inflight = true;
+                    continue;
+                }
+                if (q != cudaSuccess) {
+                    rc = cuda_status(q);
+                    break;
+                }
+                rc = collect_lane(s, L);
+                any = true;
+                if (rc) break;
+            }
+            if (rc || any || !inflight) break;
+            if (std::chrono::duration<double, std::micro>(Clock::now() - t0).count() > 250.0) {
+                std::lock_guard<std::mutex> lk(s->mu);
+                if (!s->pending.empty()) break;
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
         if (rc) fail_all(s, rc);
     }
 }
@@ -984,6 +1092,7 @@ extern "C" int sssp_serve_create(const sssp_serve_options* opt_in, sssp_server**
     sssp_server* s = new (std::nothrow) sssp_server();
     if (!s) return SSSP_E_NOMEM;
     s->opt = opt;
+    if (const char* d = std::getenv("SSSP_DEBUG")) s->debug = std::atoi(d);
     cudaGetDevice(&s->device);
     cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     size_t fr = 0, tot = 0;
