@@ -124,6 +124,27 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_sources(srcs, rank: int, ws: int) -> list:
+    """This rank's share of the sources: every ws-th one from `rank` (weak
+    scaling; the ranks' shares are disjoint and cover all sources)."""
+    mine = [int(s) for s in srcs[rank::ws]]
+    return mine or [int(srcs[0])]
+
+
+def combine_over_ranks(t_ms: float, arcs: int, verts: int, device) -> tuple:
+    """Whole-job figures: the slowest rank's time, the units all ranks
+    processed.  No-op on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_ms, arcs, verts
+    tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    at = torch.tensor([arcs, verts], dtype=torch.float64, device=device)
+    dist.all_reduce(at)
+    return float(tt.item()), int(at[0].item()), int(at[1].item())
+
+
 def cpu_oracle_gteps(g, srcs, threads: int, kind: str = "u32"):
     """The oracle as it stands: one Dijkstra per host thread, all at once."""
     import oracle
@@ -320,7 +341,8 @@ def main():
     ap.add_argument("--impl", default="mlmq", choices=["mlmq", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving/cpu legs")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--tune-ms", type=int, default=6000, help="autotune budget (0 = feature prior only)")
+    ap.add_argument("--tune-ms", type=int, default=0,
+                    help="timed autotune budget in ms (0 = the feature-based prior configuration)")
     ap.add_argument("--serve-rates", default="100,1000", help="serving leg arrival rates (q/s)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival span per rate")
     ap.add_argument("--serve-max", type=int, default=2000, help="queries per rate at most")
@@ -347,7 +369,7 @@ def main():
     tune_srcs = torch.from_numpy(srcs_all[:2].copy()).cuda()
     tuned = G.autotune(tune_srcs if args.tune_ms > 0 else None, args.tune_ms)
 
-    my_srcs = [int(s) for s in srcs_all[rank::ws]] or [int(srcs_all[0])]
+    my_srcs = rank_sources(srcs_all, rank, ws)
     stream = torch.cuda.current_stream()
     dist_t = torch.empty(g.n, dtype=torch.int32, device="cuda")
     pred_t = torch.empty(g.n, dtype=torch.int32, device="cuda")
@@ -382,13 +404,7 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     t_ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
-        at = torch.tensor([arcs, verts], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(at)
-        arcs, verts = int(at[0].item()), int(at[1].item())
+    t_ms, arcs, verts = combine_over_ranks(t_ms, arcs, verts, "cuda")
     value = arcs / (t_ms / 1e3) / 1e9
     stats = G.stats()
 

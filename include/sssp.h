@@ -159,7 +159,8 @@ typedef struct sssp_server sssp_server;
 
 /* --------------------------------------------------------- configuration -- */
 
-/* Fills *cfg with the library defaults (L1V-L2DQ-like).  SSSP_E_INVAL if cfg is NULL. */
+/* Fills *cfg with the library defaults: filtered L1 (L1FQ) over the delta-bucketed L2, four
+ * active buckets, delta derived from the weights.  SSSP_E_INVAL if cfg is NULL. */
 SSSP_API int sssp_config_default(sssp_config *cfg);
 
 /* ------------------------------------------------------------------ graph -- */

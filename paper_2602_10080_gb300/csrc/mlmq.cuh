@@ -252,6 +252,7 @@ struct BlockShared {
     unsigned long long acct;      // (held elements << 32) | unpublished L2 reads
     uint32_t scnt[32];            // elements staged per L2 bucket ring index
     unsigned long long slice_end; // serving: end of this launch's slice (globaltimer), ~0 = none
+    unsigned long long deadline;  // watchdog: globaltimer value after which waits give up
 };
 
 // ------------------------------------------------------------- watchdog --
@@ -266,6 +267,10 @@ __device__ __forceinline__ void raise_error(Ctrl* C, int code, int where, int in
 
 // ---------------------------------------------------------------- kernel --
 
+// The dynamic shared memory of mlmq_kernel (BlockShared, then the regions at
+// the byte offsets in KParams).
+extern __shared__ __align__(16) unsigned char mlmq_smem[];
+
 template <int WT, int PRED, bool MQ, int R>
 struct Worker {
     // PRED: 0 = distances only (uint32 words), 1 = (dist, pred) words with the
@@ -275,44 +280,53 @@ struct Worker {
     using A = Arith<WT>;
 
     const KParams& P;
-    BlockShared* S;
-    uint2* scratch;               // this warp's 32-element staging area
-    uint2* farbuf;                // this warp's far staging (kFarCap elements)
-    uint2* stg;                   // block staging, kStageCap elements per L2 bucket ring index
-    volatile uint2* L1;           // block L1 buffer
-    DistT* dist;
     uint32_t lane;
-    unsigned long long deadline;
-    unsigned long long slice_end;
 
     // L0 ring
     uint2 l0[R];
     uint32_t l0h, l0t;
     uint32_t nfar;                // elements in farbuf (warp-uniform)
     // deferred accounting (see acct_apply)
-    int unc;                      // private pushes (L0, far staging) not yet counted in S->acct
+    int unc;                      // private pushes (L0, far staging) not yet counted in S()->acct
     int dec;                      // completed / exported elements not yet subtracted
-    // statistics (per warp, in shared memory; lane 0 updates)
-    unsigned long long* sst;
 
-    __device__ Worker(const KParams& p, BlockShared* s, uint2* scr, uint2* far, uint2* stage, uint2* l1,
-                      unsigned long long* stats, unsigned long long dl)
-        : P(p), S(s), scratch(scr), farbuf(far), stg(stage), L1(l1), dist(reinterpret_cast<DistT*>(p.dist)),
-          lane(lane_id()), deadline(dl), slice_end(s->slice_end), l0h(0), l0t(0),
-          nfar(0), unc(0), dec(0),
-          sst(stats) {
+    // Block and warp state in shared memory, addressed from the dynamic
+    // shared array and the byte offsets in P (not kept in registers).
+    __device__ __forceinline__ uint32_t warp_id() const { return threadIdx.x >> 5; }
+    __device__ __forceinline__ BlockShared* S() const { return reinterpret_cast<BlockShared*>(mlmq_smem); }
+    // this warp's 32-element staging area
+    __device__ __forceinline__ uint2* scratch() const {
+        return reinterpret_cast<uint2*>(mlmq_smem + P.scratch_off) + warp_id() * 32u;
+    }
+    // this warp's far staging (kFarCap elements)
+    __device__ __forceinline__ uint2* farbuf() const {
+        return reinterpret_cast<uint2*>(mlmq_smem + P.far_off) + warp_id() * (uint32_t)kFarCap;
+    }
+    // block staging, kStageCap elements per L2 bucket ring index
+    __device__ __forceinline__ uint2* stg() const { return reinterpret_cast<uint2*>(mlmq_smem + P.stage_off); }
+    // block L1 buffer
+    __device__ __forceinline__ volatile uint2* L1() const {
+        return reinterpret_cast<volatile uint2*>(mlmq_smem + P.l1_off);
+    }
+    // statistics of this warp (lane 0 updates)
+    __device__ __forceinline__ unsigned long long* sst() const {
+        return reinterpret_cast<unsigned long long*>(mlmq_smem + P.stat_off) + warp_id() * (uint32_t)kStCount;
+    }
+    __device__ __forceinline__ DistT* dist() const { return reinterpret_cast<DistT*>(P.dist); }
+
+    __device__ explicit Worker(const KParams& p) : P(p), lane(lane_id()), l0h(0), l0t(0), nfar(0), unc(0), dec(0) {
         if (lane == 0)
-            for (int i = 0; i < kStCount; i++) sst[i] = 0;
+            for (int i = 0; i < kStCount; i++) sst()[i] = 0;
 #pragma unroll
         for (int r = 0; r < R; r++) l0[r] = make_uint2(0, 0);
     }
 
     // warp-uniform statistic update (lane 0 writes)
     __device__ __forceinline__ void stat(int i, unsigned long long v) const {
-        if (lane == 0) sst[i] += v;
+        if (lane == 0) sst()[i] += v;
     }
 
-    __device__ __forceinline__ bool expired() const { return gtime() > deadline; }
+    __device__ __forceinline__ bool expired() const { return gtime() > S()->deadline; }
 
     __device__ __forceinline__ bool aborted() const {
         return ld_volatile_int(&P.ctrl->error) != 0 || ld_volatile_int(&P.ctrl->finished) != 0;
@@ -350,9 +364,9 @@ struct Worker {
     // the elements can be seen; decrements may be deferred.  When the held
     // count reaches zero, the unpublished L2 reads are added to ctrl.done.
     __device__ void try_flush() {
-        unsigned long long v = *(volatile unsigned long long*)&S->acct;
+        unsigned long long v = *(volatile unsigned long long*)&S()->acct;
         while ((uint32_t)(v >> 32) == 0u && (uint32_t)v != 0u) {
-            unsigned long long old = atomicCAS(&S->acct, v, 0ull);
+            unsigned long long old = atomicCAS(&S()->acct, v, 0ull);
             if (old == v) {
                 __threadfence();
                 atomicAdd(&P.ctrl->done, (unsigned long long)(uint32_t)v);
@@ -369,15 +383,15 @@ struct Worker {
         if (lane == 0 && delta != 0) {
             __threadfence();
             unsigned long long add = ((unsigned long long)(uint32_t)delta) << 32;
-            unsigned long long old = atomicAdd(&S->acct, add);
+            unsigned long long old = atomicAdd(&S()->acct, add);
             if ((uint32_t)(old >> 32) + (uint32_t)delta == 0u) try_flush();
         }
         __syncwarp();
     }
 
     // ---- block locks ----------------------------------------------------------
-    // One warp at a time: the L1 ring (word = &S->lock) and the far-write
-    // staging (word = &S->slock) have separate locks.  Lane 0 spins on a
+    // One warp at a time: the L1 ring (word = &S()->lock) and the far-write
+    // staging (word = &S()->slock) have separate locks.  Lane 0 spins on a
     // plain read and only then tries the atomic (test-and-test-and-set),
     // with a growing sleep, so waiters do not flood the shared-memory
     // atomic unit while the holder works.
@@ -396,7 +410,7 @@ struct Worker {
                 __nanosleep(ns);
                 ns = ns < 256u ? ns * 2u : 256u;
             }
-            sst[kStLockSpin] += spins;
+            sst()[kStLockSpin] += spins;
         }
         ok = __shfl_sync(kFull, ok, 0);
         __threadfence_block();
@@ -408,10 +422,10 @@ struct Worker {
         if (lane == 0) atomicExch(word, 0);
         __syncwarp();
     }
-    __device__ __forceinline__ bool lock() { return lock(&S->lock); }
-    __device__ __forceinline__ void unlock() { unlock(&S->lock); }
-    __device__ __forceinline__ bool slock() { return lock(&S->slock); }
-    __device__ __forceinline__ void sunlock() { unlock(&S->slock); }
+    __device__ __forceinline__ bool lock() { return lock(&S()->lock); }
+    __device__ __forceinline__ void unlock() { unlock(&S()->lock); }
+    __device__ __forceinline__ bool slock() { return lock(&S()->slock); }
+    __device__ __forceinline__ void sunlock() { unlock(&S()->slock); }
 
     // ---- L2: sharded bucket rings -----------------------------------------
     __device__ __forceinline__ unsigned long long window() const {
@@ -490,7 +504,7 @@ struct Worker {
                     }
                     __nanosleep(32);
                 }
-                if (spins) atomicAdd(&sst[kStWaitSpin], (unsigned long long)spins);
+                if (spins) atomicAdd(&sst()[kStWaitSpin], (unsigned long long)spins);
             }
         }
         const int ldr = __ffs(grp) - 1;
@@ -586,7 +600,7 @@ struct Worker {
                         rr = old;
                         w = ld_relaxed(P.l2.wt + (size_t)ring * 32);
                     }
-                    if (!got) atomicAdd((unsigned long long*)&sst[kStCasFail], 1ull);
+                    if (!got) atomicAdd((unsigned long long*)&sst()[kStCasFail], 1ull);
                 }
                 got = __shfl_sync(kFull, got, c);
                 if (got) {
@@ -619,7 +633,7 @@ struct Worker {
                 }
                 __nanosleep(32);
             }
-            if (spins) atomicAdd(&sst[kStWaitSpin], (unsigned long long)spins);
+            if (spins) atomicAdd(&sst()[kStWaitSpin], (unsigned long long)spins);
             if (ok) cnt = P.l2.cnt[slot];
         }
         okr = __all_sync(kFull, ok != 0);
@@ -654,30 +668,30 @@ struct Worker {
         if (type == 1) {
             // near-far: two rings of cap/2
             const uint32_t half = cap >> 1;
-            uint32_t nf = sread(&S->nf);
+            uint32_t nf = sread(&S()->nf);
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 bool nearv = valid[k] && e[k].y < nf;
                 bool farv = valid[k] && !nearv;
                 uint32_t nm = __ballot_sync(kFull, nearv), fm = __ballot_sync(kFull, farv);
-                uint32_t h = sread(&S->head), t = sread(&S->tail);
-                uint32_t fh = sread(&S->fhead), ft = sread(&S->ftail);
+                uint32_t h = sread(&S()->head), t = sread(&S()->tail);
+                uint32_t fh = sread(&S()->fhead), ft = sread(&S()->ftail);
                 uint32_t nspace = half - (t - h), fspace = half - (ft - fh);
                 uint32_t nr = __popc(nm & lanemask_lt()), fr = __popc(fm & lanemask_lt());
                 out[k] = false;
                 if (nearv) {
-                    if (nr < nspace) vst(&L1[(t + nr) & (half - 1u)], e[k]);
+                    if (nr < nspace) vst(&L1()[(t + nr) & (half - 1u)], e[k]);
                     else out[k] = true;
                 }
                 if (farv) {
-                    if (fr < fspace) vst(&L1[half + ((ft + fr) & (half - 1u))], e[k]);
+                    if (fr < fspace) vst(&L1()[half + ((ft + fr) & (half - 1u))], e[k]);
                     else out[k] = true;
                 }
                 __syncwarp();
                 if (lane == 0) {
                     uint32_t nn = __popc(nm), fn = __popc(fm);
-                    *(volatile uint32_t*)&S->tail = t + (nn < nspace ? nn : nspace);
-                    *(volatile uint32_t*)&S->ftail = ft + (fn < fspace ? fn : fspace);
+                    *(volatile uint32_t*)&S()->tail = t + (nn < nspace ? nn : nspace);
+                    *(volatile uint32_t*)&S()->ftail = ft + (fn < fspace ? fn : fspace);
                 }
                 __syncwarp();
             }
@@ -685,9 +699,9 @@ struct Worker {
             // SLF deque: dist <= head element -> push front, else push back
 #pragma unroll
             for (int k = 0; k < K; k++) {
-                uint32_t h = sread(&S->head), t = sread(&S->tail);
+                uint32_t h = sread(&S()->head), t = sread(&S()->tail);
                 uint32_t hd = 0;
-                if (lane == 0 && t != h) hd = vld(&L1[h & l1_mask()]).y;
+                if (lane == 0 && t != h) hd = vld(&L1()[h & l1_mask()]).y;
                 hd = __shfl_sync(kFull, hd, 0);
                 bool front = valid[k] && t != h && e[k].y <= hd;
                 bool back = valid[k] && !front;
@@ -699,17 +713,17 @@ struct Worker {
                 uint32_t fr = __popc(fm & lanemask_lt()), br = __popc(bm & lanemask_lt());
                 out[k] = false;
                 if (front) {
-                    if (fr < ftake) vst(&L1[(h - 1u - fr) & l1_mask()], e[k]);
+                    if (fr < ftake) vst(&L1()[(h - 1u - fr) & l1_mask()], e[k]);
                     else out[k] = true;
                 }
                 if (back) {
-                    if (br < btake) vst(&L1[(t + br) & l1_mask()], e[k]);
+                    if (br < btake) vst(&L1()[(t + br) & l1_mask()], e[k]);
                     else out[k] = true;
                 }
                 __syncwarp();
                 if (lane == 0) {
-                    *(volatile uint32_t*)&S->head = h - ftake;
-                    *(volatile uint32_t*)&S->tail = t + btake;
+                    *(volatile uint32_t*)&S()->head = h - ftake;
+                    *(volatile uint32_t*)&S()->tail = t + btake;
                 }
                 __syncwarp();
             }
@@ -722,24 +736,24 @@ struct Worker {
                 bool want = valid[k] &&
                             (type != 2 || (MQ && P.qoff ? abs_bucket(e[k].x, e[k].y) <= fthr : e[k].y <= fthr));
                 uint32_t wm = __ballot_sync(kFull, want);
-                uint32_t h = sread(&S->head), t = sread(&S->tail);
+                uint32_t h = sread(&S()->head), t = sread(&S()->tail);
                 uint32_t space = cap - (t - h);
                 uint32_t rank = __popc(wm & lanemask_lt());
                 out[k] = valid[k] && !want;
                 if (want) {
-                    if (rank < space) vst(&L1[(t + rank) & l1_mask()], e[k]);
+                    if (rank < space) vst(&L1()[(t + rank) & l1_mask()], e[k]);
                     else out[k] = true;
                 }
                 __syncwarp();
                 if (lane == 0) {
                     uint32_t c = __popc(wm);
-                    *(volatile uint32_t*)&S->tail = t + (c < space ? c : space);
+                    *(volatile uint32_t*)&S()->tail = t + (c < space ? c : space);
                 }
                 __syncwarp();
             }
         }
         if (lane == 0 && count_add != 0)
-            atomicAdd(&S->acct, ((unsigned long long)(uint32_t)count_add) << 32);
+            atomicAdd(&S()->acct, ((unsigned long long)(uint32_t)count_add) << 32);
     }
 
     // Moves everything in L1 to L2 (periodic flush of L1V, Section 3.4).
@@ -749,14 +763,14 @@ struct Worker {
         if (P.l1_type == 1) {
             const uint32_t half = cap >> 1;
             for (int rg = 0; rg < 2; rg++) {
-                uint32_t* hp = rg ? &S->fhead : &S->head;
-                uint32_t* tp = rg ? &S->ftail : &S->tail;
+                uint32_t* hp = rg ? &S()->fhead : &S()->head;
+                uint32_t* tp = rg ? &S()->ftail : &S()->tail;
                 uint32_t h = sread(hp), t = sread(tp);
                 while (h != t) {
                     uint32_t c = t - h < 32u ? t - h : 32u;
                     bool v = lane < c;
                     uint2 x = make_uint2(0, 0);
-                    if (v) x = vld(&L1[(rg ? half : 0u) + ((h + lane) & (half - 1u))]);
+                    if (v) x = vld(&L1()[(rg ? half : 0u) + ((h + lane) & (half - 1u))]);
                     h += c;
                     dec += l2_write(v, x);
                 }
@@ -765,17 +779,17 @@ struct Worker {
                 __syncwarp();
             }
         } else {
-            uint32_t h = sread(&S->head), t = sread(&S->tail);
+            uint32_t h = sread(&S()->head), t = sread(&S()->tail);
             while (h != t) {
                 uint32_t c = t - h < 32u ? t - h : 32u;
                 bool v = lane < c;
                 uint2 x = make_uint2(0, 0);
-                if (v) x = vld(&L1[(h + lane) & l1_mask()]);
+                if (v) x = vld(&L1()[(h + lane) & l1_mask()]);
                 h += c;
                 dec += l2_write(v, x);
             }
             __syncwarp();
-            if (lane == 0) *(volatile uint32_t*)&S->head = h;
+            if (lane == 0) *(volatile uint32_t*)&S()->head = h;
             __syncwarp();
         }
         stat(kStFlush, 1);
@@ -796,7 +810,7 @@ struct Worker {
         const uint32_t cap = (uint32_t)P.l1_cap;
         // the elements become visible to other warps: count them first
         if (lane == 0 && count_add != 0)
-            atomicAdd(&S->acct, ((unsigned long long)(uint32_t)count_add) << 32);
+            atomicAdd(&S()->acct, ((unsigned long long)(uint32_t)count_add) << 32);
         __syncwarp();
         bool out[K];
 #pragma unroll
@@ -809,13 +823,13 @@ struct Worker {
             const uint32_t c = __popc(wm);
             uint32_t base = 0, take = 0;
             if (lane == 0) {
-                uint32_t t = *(volatile uint32_t*)&S->tail;
+                uint32_t t = *(volatile uint32_t*)&S()->tail;
                 for (;;) {
-                    const uint32_t h = *(volatile uint32_t*)&S->head;
+                    const uint32_t h = *(volatile uint32_t*)&S()->head;
                     const uint32_t used = t - h;
                     take = used < cap ? min(c, cap - used) : 0u;
                     if (take == 0) break;
-                    const uint32_t old = atomicCAS(&S->tail, t, t + take);
+                    const uint32_t old = atomicCAS(&S()->tail, t, t + take);
                     if (old == t) break;
                     t = old;
                 }
@@ -828,7 +842,7 @@ struct Worker {
             out[k] = out[k] || (want && !placed);
             int ok = 1;
             if (placed) {
-                volatile uint2* slot = &L1[(base + rank) & l1_mask()];
+                volatile uint2* slot = &L1()[(base + rank) & l1_mask()];
                 uint32_t spins = 0;
                 while (vld(slot).x != kEmptyKey) {
                     if ((++spins & 255u) == 0 && expired()) {
@@ -849,12 +863,12 @@ struct Worker {
         valid = false;
         uint32_t h = 0, c = 0;
         if (lane == 0) {
-            h = *(volatile uint32_t*)&S->head;
+            h = *(volatile uint32_t*)&S()->head;
             for (;;) {
-                const uint32_t t = *(volatile uint32_t*)&S->tail;
+                const uint32_t t = *(volatile uint32_t*)&S()->tail;
                 c = t - h < 32u ? t - h : 32u;
                 if (c == 0) break;
-                const uint32_t old = atomicCAS(&S->head, h, h + c);
+                const uint32_t old = atomicCAS(&S()->head, h, h + c);
                 if (old == h) break;
                 h = old;
             }
@@ -863,7 +877,7 @@ struct Worker {
         if (c == 0) return false;
         h = __shfl_sync(kFull, h, 0);
         if (lane < c) {
-            volatile uint2* slot = &L1[(h + lane) & l1_mask()];
+            volatile uint2* slot = &L1()[(h + lane) & l1_mask()];
             uint32_t spins = 0;
             uint2 x = vld(slot);
             while (x.x == kEmptyKey) {
@@ -901,7 +915,7 @@ struct Worker {
             if (P.wb > 0) {
                 // L1V periodic flush (Section 3.4): every wb-th write moves L1 to L2
                 uint32_t wc = 0;
-                if (lane == 0) wc = atomicAdd(&S->writes, 1u) + 1u;
+                if (lane == 0) wc = atomicAdd(&S()->writes, 1u) + 1u;
                 wc = __shfl_sync(kFull, wc, 0);
                 if (wc % (uint32_t)P.wb == 0u) {
                     bool v = false;
@@ -921,8 +935,8 @@ struct Worker {
         if (P.wb > 0) {
             uint32_t wcount = 0;
             if (lane == 0) {
-                wcount = *(volatile uint32_t*)&S->writes + 1u;
-                *(volatile uint32_t*)&S->writes = wcount;
+                wcount = *(volatile uint32_t*)&S()->writes + 1u;
+                *(volatile uint32_t*)&S()->writes = wcount;
             }
             wcount = __shfl_sync(kFull, wcount, 0);
             flush = (wcount % (uint32_t)P.wb) == 0u;
@@ -940,22 +954,22 @@ struct Worker {
         // cheap unlocked emptiness test first (lane 0 decides for the warp)
         uint32_t any = 0;
         if (lane == 0) {
-            any = *(volatile uint32_t*)&S->head != *(volatile uint32_t*)&S->tail;
-            if (P.l1_type == 1) any |= *(volatile uint32_t*)&S->fhead != *(volatile uint32_t*)&S->ftail;
+            any = *(volatile uint32_t*)&S()->head != *(volatile uint32_t*)&S()->tail;
+            if (P.l1_type == 1) any |= *(volatile uint32_t*)&S()->fhead != *(volatile uint32_t*)&S()->ftail;
         }
         if (!__shfl_sync(kFull, any, 0)) return false;
         if (l1_lockfree()) return l1_read_lf(valid, e);
         if (!lock()) return false;
         const uint32_t cap = (uint32_t)P.l1_cap;
-        uint32_t h = sread(&S->head), t = sread(&S->tail);
+        uint32_t h = sread(&S()->head), t = sread(&S()->tail);
         if (P.l1_type == 1 && h == t) {
             // near vector drained: NF = min(far) + delta, then re-partition far
             const uint32_t half = cap >> 1;
-            uint32_t fh = sread(&S->fhead), ft = sread(&S->ftail);
+            uint32_t fh = sread(&S()->fhead), ft = sread(&S()->ftail);
             if (fh != ft) {
                 uint32_t mn = kInfU32;
                 for (uint32_t i = fh + lane; i - fh < ft - fh; i += 32)
-                    mn = min(mn, vld(&L1[half + (i & (half - 1u))]).y);
+                    mn = min(mn, vld(&L1()[half + (i & (half - 1u))]).y);
                 mn = __reduce_min_sync(kFull, mn);
                 uint32_t nf = A::plus_delta(mn, P.delta);
                 uint32_t nt = t, nft = ft;
@@ -963,22 +977,22 @@ struct Worker {
                 for (uint32_t base = 0; base < count; base += 32) {
                     bool v = base + lane < count;
                     uint2 x = make_uint2(0, 0);
-                    if (v) x = vld(&L1[half + ((fh + base + lane) & (half - 1u))]);
+                    if (v) x = vld(&L1()[half + ((fh + base + lane) & (half - 1u))]);
                     __syncwarp();
                     bool nearv = v && x.y < nf;
                     bool farv = v && !nearv;
                     uint32_t nm = __ballot_sync(kFull, nearv), fm = __ballot_sync(kFull, farv);
-                    if (nearv) vst(&L1[(nt + __popc(nm & lanemask_lt())) & (half - 1u)], x);
-                    if (farv) vst(&L1[half + ((nft + __popc(fm & lanemask_lt())) & (half - 1u))], x);
+                    if (nearv) vst(&L1()[(nt + __popc(nm & lanemask_lt())) & (half - 1u)], x);
+                    if (farv) vst(&L1()[half + ((nft + __popc(fm & lanemask_lt())) & (half - 1u))], x);
                     __syncwarp();
                     nt += __popc(nm);
                     nft += __popc(fm);
                 }
                 if (lane == 0) {
-                    *(volatile uint32_t*)&S->nf = nf;
-                    *(volatile uint32_t*)&S->tail = nt;
-                    *(volatile uint32_t*)&S->fhead = fh + count;
-                    *(volatile uint32_t*)&S->ftail = nft;
+                    *(volatile uint32_t*)&S()->nf = nf;
+                    *(volatile uint32_t*)&S()->tail = nt;
+                    *(volatile uint32_t*)&S()->fhead = fh + count;
+                    *(volatile uint32_t*)&S()->ftail = nft;
                 }
                 __syncwarp();
                 t = nt;
@@ -988,10 +1002,10 @@ struct Worker {
         valid = lane < c;
         if (valid) {
             uint32_t idx = P.l1_type == 1 ? ((h + lane) & ((cap >> 1) - 1u)) : ((h + lane) & l1_mask());
-            e = vld(&L1[idx]);
+            e = vld(&L1()[idx]);
         }
         __syncwarp();
-        if (lane == 0) *(volatile uint32_t*)&S->head = h + c;
+        if (lane == 0) *(volatile uint32_t*)&S()->head = h + c;
         unlock();
         if (c) stat(kStPopL1, 1);
         return c != 0;
@@ -1001,7 +1015,7 @@ struct Worker {
     __device__ uint32_t l1_free() const {
         uint32_t f = 0;
         if (lane == 0) {
-            uint32_t h = *(volatile uint32_t*)&S->head, t = *(volatile uint32_t*)&S->tail;
+            uint32_t h = *(volatile uint32_t*)&S()->head, t = *(volatile uint32_t*)&S()->tail;
             uint32_t cap = (uint32_t)P.l1_cap >> (P.l1_type == 1 ? 1 : 0);
             uint32_t used = t - h;
             f = used < cap ? cap - used : 0u;
@@ -1018,8 +1032,8 @@ struct Worker {
         valid = false;
         int role = 0;
         if (lane == 0) {
-            role = atomicAdd(&S->refill, 1) < P.refillers;
-            if (!role) atomicSub(&S->refill, 1);
+            role = atomicAdd(&S()->refill, 1) < P.refillers;
+            if (!role) atomicSub(&S()->refill, 1);
         }
         role = __shfl_sync(kFull, role, 0);
         if (!role) return -1;
@@ -1039,7 +1053,7 @@ struct Worker {
                 // them before they can be handed to other warps through L1
                 const uint32_t total = __reduce_add_sync(kFull, cnt);
                 if (lane == 0)
-                    atomicAdd(&S->acct, ((unsigned long long)total << 32) | (unsigned long long)total);
+                    atomicAdd(&S()->acct, ((unsigned long long)total << 32) | (unsigned long long)total);
                 const uint32_t c0 = __shfl_sync(kFull, cnt, 0);
                 l2_read_chunk(ring, t, c0, valid, e);
                 for (uint32_t j = 1; j < got; j++) {
@@ -1057,7 +1071,7 @@ struct Worker {
             }
         }
         __syncwarp();
-        if (lane == 0) atomicSub(&S->refill, 1);
+        if (lane == 0) atomicSub(&S()->refill, 1);
         __syncwarp();
         return result;
     }
@@ -1098,7 +1112,7 @@ struct Worker {
         l1_write<R>(e, v, add);
     }
 
-    // Appends c (<= 32) staged elements scratch[0..c) to L0.  `counted`:
+    // Appends c (<= 32) staged elements scratch()[0..c) to L0.  `counted`:
     // they are already in the block count (a deferred batch element).
     __device__ void l0_push(uint32_t c, bool counted = false) {
         if (c == 0) return;
@@ -1106,7 +1120,7 @@ struct Worker {
         uint32_t k = (lane - l0t) & 31u;
         if (k < c) {
             uint32_t p = l0t + k;
-            l0_set((p >> 5) & (R - 1u), scratch[k]);
+            l0_set((p >> 5) & (R - 1u), scratch()[k]);
         }
         l0t += c;
         if (!counted) unc += (int)c;
@@ -1151,12 +1165,12 @@ struct Worker {
 
     // Takes up to 32 staged elements of bucket ring index b (lock held).
     __device__ uint32_t stage_take(uint32_t b, bool& v, uint2& x) {
-        const uint32_t c0 = sread(&S->scnt[b]);
+        const uint32_t c0 = sread(&S()->scnt[b]);
         const uint32_t c = c0 < 32u ? c0 : 32u;
         v = lane < c;
-        if (v) x = stg[b * kStageCap + (c0 - c) + lane];
+        if (v) x = stg()[b * kStageCap + (c0 - c) + lane];
         __syncwarp();
-        if (lane == 0) S->scnt[b] = c0 - c;
+        if (lane == 0) S()->scnt[b] = c0 - c;
         __syncwarp();
         return c;
     }
@@ -1174,7 +1188,7 @@ struct Worker {
             const uint32_t b = lane;
             const bool cand = b < (uint32_t)P.bmax &&
                               (all || b == W % (uint32_t)P.bmax || b == (W + 1u) % (uint32_t)P.bmax);
-            if (cand) cnt = *(volatile uint32_t*)&S->scnt[b];
+            if (cand) cnt = *(volatile uint32_t*)&S()->scnt[b];
             const uint32_t m = __ballot_sync(kFull, cand && cnt > 0u);
             if (!m) return;
             const uint32_t bf = (uint32_t)(__ffs(m) - 1);
@@ -1196,7 +1210,7 @@ struct Worker {
             const uint32_t take = nfar - upto < 32u ? nfar - upto : 32u;
             const bool v = lane < take;
             uint2 x = make_uint2(0, 0);
-            if (v) x = farbuf[nfar - take + lane];
+            if (v) x = farbuf()[nfar - take + lane];
             __syncwarp();
             nfar -= take;
             if (!P.stage) {
@@ -1214,19 +1228,19 @@ struct Worker {
             if (!slock()) return;
             // the staged elements become visible to the block: count every
             // private push now (counting early only delays the done flush)
-            if (lane == 0 && unc != 0) atomicAdd(&S->acct, ((unsigned long long)(uint32_t)unc) << 32);
+            if (lane == 0 && unc != 0) atomicAdd(&S()->acct, ((unsigned long long)(uint32_t)unc) << 32);
             unc = 0;
             const uint32_t grp = __match_any_sync(kFull, sv ? b : 0xffffffffu);
             const int ldr = __ffs(grp) - 1;
             uint32_t base = 0;
-            if (sv && lane == (uint32_t)ldr) base = S->scnt[b];
+            if (sv && lane == (uint32_t)ldr) base = S()->scnt[b];
             base = __shfl_sync(kFull, base, ldr);
             const uint32_t rank = __popc(grp & lanemask_lt());
             over = sv && base + rank >= (uint32_t)kStageCap;
-            if (sv && !over) stg[b * kStageCap + base + rank] = x;
+            if (sv && !over) stg()[b * kStageCap + base + rank] = x;
             const uint32_t placed = min((uint32_t)__popc(grp), (uint32_t)kStageCap - min(base, (uint32_t)kStageCap));
             const bool full = sv && lane == (uint32_t)ldr && base + placed >= 32u;
-            if (sv && lane == (uint32_t)ldr) S->scnt[b] = base + placed;
+            if (sv && lane == (uint32_t)ldr) S()->scnt[b] = base + placed;
             __syncwarp();
             const uint32_t fm = __ballot_sync(kFull, full);
             if (fm) {
@@ -1244,7 +1258,7 @@ struct Worker {
         if (!m) return;
         uint32_t c = __popc(m);
         if (nfar + c > (uint32_t)kFarCap) far_flush(0);
-        if (f) farbuf[nfar + __popc(m & lanemask_lt())] = x;
+        if (f) farbuf()[nfar + __popc(m & lanemask_lt())] = x;
         __syncwarp();
         nfar += c;
         unc += (int)c;
@@ -1260,20 +1274,20 @@ struct Worker {
                                           uint32_t& nd) {
         nd = A::add(du, wbits);
         if (PRED == 0) {
-            uint32_t* p = reinterpret_cast<uint32_t*>(dist) + vidx;
+            uint32_t* p = reinterpret_cast<uint32_t*>(dist()) + vidx;
             uint32_t cur = ld_dist(p);
             if (nd >= cur) return false;
             uint32_t old = atomicMin(p, nd);
             return old > nd;
         } else if (PRED == 1) {
-            unsigned long long* p = reinterpret_cast<unsigned long long*>(dist) + vidx;
+            unsigned long long* p = reinterpret_cast<unsigned long long*>(dist()) + vidx;
             unsigned long long cand = ((unsigned long long)nd << 32) | u;
             unsigned long long cur = ld_dist(p);
             if (cand >= cur) return false;
             unsigned long long old = atomicMin(p, cand);
             return (uint32_t)(old >> 32) > nd;
         } else {
-            unsigned long long* p = reinterpret_cast<unsigned long long*>(dist) + vidx;
+            unsigned long long* p = reinterpret_cast<unsigned long long*>(dist()) + vidx;
             unsigned long long cand = ((unsigned long long)nd << 32) | u;
             unsigned long long cur = ld_dist(p);
             while ((uint32_t)(cur >> 32) > nd) {
@@ -1296,15 +1310,15 @@ struct Worker {
         nd = A::add(du, wbits);
         if (PRED == 0) {
             if (nd >= (uint32_t)cur) return false;
-            atomicMin(reinterpret_cast<uint32_t*>(dist) + vidx, nd);
+            atomicMin(reinterpret_cast<uint32_t*>(dist()) + vidx, nd);
             return true;
         } else if (PRED == 1) {
             const unsigned long long cand = ((unsigned long long)nd << 32) | u;
             if (cand >= (unsigned long long)cur) return false;
-            atomicMin(reinterpret_cast<unsigned long long*>(dist) + vidx, cand);
+            atomicMin(reinterpret_cast<unsigned long long*>(dist()) + vidx, cand);
             return (uint32_t)((unsigned long long)cur >> 32) > nd;
         } else {
-            unsigned long long* p = reinterpret_cast<unsigned long long*>(dist) + vidx;
+            unsigned long long* p = reinterpret_cast<unsigned long long*>(dist()) + vidx;
             const unsigned long long cand = ((unsigned long long)nd << 32) | u;
             unsigned long long c = (unsigned long long)cur;
             while ((uint32_t)(c >> 32) > nd) {
@@ -1325,7 +1339,7 @@ struct Worker {
         const bool nearv = imp && w <= P.near_w && key_vertex(key) < (uint32_t)P.n;
         const uint32_t m = __ballot_sync(kFull, nearv);
         if (m) {
-            if (nearv) scratch[__popc(m & lanemask_lt())] = make_uint2(key, nd);
+            if (nearv) scratch()[__popc(m & lanemask_lt())] = make_uint2(key, nd);
             __syncwarp();
             l0_push(__popc(m));
         }
@@ -1379,7 +1393,7 @@ struct Worker {
             valid = false;
         }
         if (valid) {
-            uint32_t cur = dpart(ld_dist(dist + dist_index(key)));
+            uint32_t cur = dpart(ld_dist(dist() + dist_index(key)));
             if (du > cur) {
                 valid = false;
                 stale = true;
@@ -1403,7 +1417,7 @@ struct Worker {
         const bool defer = valid && ex >= P.max_arcs;
         const uint32_t dm = __ballot_sync(kFull, defer);
         if (dm) {
-            if (defer) scratch[__popc(dm & lanemask_lt())] = el;
+            if (defer) scratch()[__popc(dm & lanemask_lt())] = el;
             __syncwarp();
             l0_push(__popc(dm), true);
             consumed -= __popc(dm);
@@ -1446,7 +1460,7 @@ struct Worker {
             bool imp = false;
             if (cu.in) {
                 const size_t vidx = MQ ? (size_t)cu.q * (size_t)P.nv + cu.a.x : (size_t)cu.a.x;
-                imp = relax_cur(vidx, cu.pu, cu.du, cu.a.y, ld_dist(dist + vidx), nd);
+                imp = relax_cur(vidx, cu.pu, cu.du, cu.a.y, ld_dist(dist() + vidx), nd);
             }
             push_round(imp, MQ ? ((cu.q << P.vbits) | cu.a.x) : cu.a.x, nd, cu.a.y);
         }
@@ -1456,7 +1470,7 @@ struct Worker {
     __device__ __noinline__ void publish_stats() {
         if (lane == 0) {
             for (int i = 0; i < kStCount; i++)
-                if (sst[i]) atomicAdd(&P.ctrl->stats[i], sst[i]);
+                if (sst()[i]) atomicAdd(&P.ctrl->stats[i], sst()[i]);
         }
     }
 
@@ -1475,7 +1489,7 @@ struct Worker {
                         raise_error(P.ctrl, kErrTimeout, 7, 0);
                         stop = 1;
                     }
-                    if (!stop && gtime() > slice_end) stop = 2;  // end of a serving slice
+                    if (!stop && gtime() > S()->slice_end) stop = 2;  // end of a serving slice
                 }
                 stop = __shfl_sync(kFull, stop, 0);
                 if (stop) break;
@@ -1571,14 +1585,14 @@ struct Worker {
             if (P.l1_type == 1) {
                 const uint32_t half = (uint32_t)P.l1_cap >> 1;
                 for (int rg = 0; rg < 2; rg++) {
-                    uint32_t* hp = rg ? &S->fhead : &S->head;
-                    uint32_t* tp = rg ? &S->ftail : &S->tail;
+                    uint32_t* hp = rg ? &S()->fhead : &S()->head;
+                    uint32_t* tp = rg ? &S()->ftail : &S()->tail;
                     uint32_t h = sread(hp), t = sread(tp);
                     while (h != t) {
                         const uint32_t c = t - h < 32u ? t - h : 32u;
                         const bool v = lane < c;
                         uint2 x = make_uint2(0, 0);
-                        if (v) x = vld(&L1[(rg ? half : 0u) + ((h + lane) & (half - 1u))]);
+                        if (v) x = vld(&L1()[(rg ? half : 0u) + ((h + lane) & (half - 1u))]);
                         h += c;
                         dec += l2_write(v, x);
                     }
@@ -1586,16 +1600,16 @@ struct Worker {
                     __syncwarp();
                 }
             } else {
-                uint32_t h = sread(&S->head), t = sread(&S->tail);
+                uint32_t h = sread(&S()->head), t = sread(&S()->tail);
                 while (h != t) {
                     const uint32_t c = t - h < 32u ? t - h : 32u;
                     const bool v = lane < c;
                     uint2 x = make_uint2(0, 0);
-                    if (v) x = vld(&L1[(h + lane) & l1_mask()]);
+                    if (v) x = vld(&L1()[(h + lane) & l1_mask()]);
                     h += c;
                     dec += l2_write(v, x);
                 }
-                if (lane == 0) *(volatile uint32_t*)&S->head = h;
+                if (lane == 0) *(volatile uint32_t*)&S()->head = h;
                 __syncwarp();
             }
             unlock();
@@ -1605,7 +1619,7 @@ struct Worker {
         if (lane == 0) {
             // nothing may stay behind in the block: its count must be zero,
             // and the L2 reads it finished are published to ctrl.done
-            const unsigned long long v = *(volatile unsigned long long*)&S->acct;
+            const unsigned long long v = *(volatile unsigned long long*)&S()->acct;
             if ((uint32_t)(v >> 32) != 0u) raise_error(P.ctrl, kErrState, 9, (int)(v >> 32));
             else try_flush();
         }
@@ -1615,13 +1629,8 @@ struct Worker {
 
 template <int WT, int PRED, bool MQ, int R>
 __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    BlockShared* S = reinterpret_cast<BlockShared*>(smem);
-    uint2* scratch_all = reinterpret_cast<uint2*>(smem + P.scratch_off);
-    uint2* far_all = reinterpret_cast<uint2*>(smem + P.far_off);
-    uint2* l1 = reinterpret_cast<uint2*>(smem + P.l1_off);
-    unsigned long long* stats_all = reinterpret_cast<unsigned long long*>(smem + P.stat_off);
-    uint2* stage = reinterpret_cast<uint2*>(smem + P.stage_off);
+    BlockShared* S = reinterpret_cast<BlockShared*>(mlmq_smem);
+    volatile uint2* l1 = reinterpret_cast<volatile uint2*>(mlmq_smem + P.l1_off);
     if (threadIdx.x == 0) {
         S->lock = 0;
         S->slock = 0;
@@ -1632,6 +1641,7 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
         for (int i = 0; i < 32; i++) S->scnt[i] = 0;
         unsigned long long win = ld_acquire64(&P.ctrl->window);
         S->nf = Arith<WT>::upper((uint32_t)win, P.delta, 1.0f);
+        S->deadline = gtime() + P.timeout_ns;
         S->slice_end = ~0ull;
         if (P.slice_ns) {
             // the first block to start fixes the slice's end for all blocks
@@ -1642,16 +1652,13 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
     }
     for (int i = threadIdx.x; i < P.l1_cap; i += blockDim.x) vst(l1 + i, make_uint2(kEmptyKey, 0u));
     __syncthreads();
-    const unsigned long long deadline = gtime() + P.timeout_ns;
-    const int warp = threadIdx.x >> 5;
-    Worker<WT, PRED, MQ, R> w(P, S, scratch_all + warp * 32, far_all + warp * kFarCap, stage, l1,
-                              stats_all + warp * kStCount, deadline);
+    Worker<WT, PRED, MQ, R> w(P);
     w.run();
     if (P.slice_ns) {
         // serving slice: every warp has drained its private state; one warp
         // now drains what the block shares
         __syncthreads();
-        if (warp == 0) w.drain_block();
+        if ((threadIdx.x >> 5) == 0) w.drain_block();
     }
 }
 

@@ -401,7 +401,7 @@ static void config_defaults(sssp_config* c) {
     c->wb = 0;
     c->delta_u32 = 0;     // 0 = derive from the graph's weights
     c->delta_f32 = 0.0f;
-    c->bnum = 2;
+    c->bnum = 4;
     c->bmax = 32;
     c->filter_deltas = 1.0f;
     c->near_deltas = 1.0f;

@@ -43,7 +43,7 @@ sssp_config prior_config(const Graph* g) {
             c.l2_type = SSSP_L2_BUCKET;
             c.filter_deltas = 1.0f;
             c.near_deltas = 1.0f;
-            c.bnum = 2;
+            c.bnum = 4;
             break;
         case kMesh:
             c.l1_type = SSSP_L1_FILTER;
