@@ -57,6 +57,16 @@ constexpr int kChunk = 32;          // elements per L2 chunk
 constexpr int kFarCap = 64;         // per-warp far staging (elements)
 constexpr int kMaxClaim = 8;        // chunks per L2 claim (upper bound)
 constexpr int kStageCap = 64;       // block staging per L2 bucket (elements)
+#ifndef SSSP_WINDOW_GUARD
+#define SSSP_WINDOW_GUARD 8
+#endif
+#ifndef SSSP_FRONT_BOUND
+#define SSSP_FRONT_BOUND 1
+#endif
+constexpr uint32_t kWindowGuard = SSSP_WINDOW_GUARD;  // buckets kept clear at the far end of the L2 window
+#ifndef SSSP_PIPELINE
+#define SSSP_PIPELINE 0
+#endif
 constexpr uint32_t kInfU32 = 0xffffffffu;
 constexpr uint32_t kEmptyKey = 0xffffffffu;  // a free L1 slot (never a valid element key)
 constexpr uint32_t kSatU32 = 0xfffffffeu;
@@ -78,6 +88,7 @@ enum : int {
     // SM clock cycles spent per phase (lane 0 of every warp, summed)
     kCyRelax, kCyL1, kCyL2Write, kCyGlobalRead, kCyIdle, kCyL0,
     kStLockSpin, kStWaitSpin, kStIdleIter, kStRefillTry, kStIter, kStRounds,
+    kStPullBack, kStLowWrite, kStAdvance,
     kStCount
 };
 
@@ -138,7 +149,15 @@ struct KParams {
     unsigned long long slice_ns;   // serving: end the launch after this long, draining local queues to L2 (0 = run to completion)
     const uint32_t* qoff;          // serving: per-query bucket offset (the window position when the query was admitted), or null
     unsigned long long* trace;   // debug only: per-lane (location << 48 | iteration), mapped host memory
+    unsigned long long* timeline; // run-time sampling (or null): kTimelineFields words per sample
+    int32_t timeline_cap;         // samples that fit
+    uint32_t timeline_ns;         // sampling period
 };
+
+// Run-time sampling (one lane of block 0): time since start, elements
+// written to L2 (reserve), L2 elements completed (done), the window W, and
+// the warps of block 0 that held a batch at the sampling instant.
+constexpr int kTimelineFields = 5;
 
 // ------------------------------------------------------------------ PTX --
 
@@ -253,6 +272,10 @@ struct BlockShared {
     uint32_t scnt[32];            // elements staged per L2 bucket ring index
     unsigned long long slice_end; // serving: end of this launch's slice (globaltimer), ~0 = none
     unsigned long long deadline;  // watchdog: globaltimer value after which waits give up
+    unsigned long long t0;        // launch start (globaltimer), for run-time sampling
+    unsigned long long next_sample;
+    uint32_t nsamples;
+    uint32_t busy;                // warps of the block holding a batch (sampling only)
 };
 
 // ------------------------------------------------------------- watchdog --
@@ -458,9 +481,9 @@ struct Worker {
         win = __shfl_sync(kFull, win, 0);
         const uint32_t W = (uint32_t)win;
         const uint32_t shard = home_shard();
-        // absolute bucket; beyond the window span -> the window's last bucket
+        // absolute bucket (clamp_bucket: beyond the window's reach -> its far end)
         uint32_t ab = valid ? abs_bucket(e.x, e.y) : W;
-        if (ab > W && ab - W >= (uint32_t)P.bmax) ab = W + (uint32_t)P.bmax - 1u;
+        ab = clamp_bucket(ab, W);
         const uint32_t b = ab % (uint32_t)P.bmax;
         const uint32_t below = __reduce_min_sync(kFull, valid ? ab : 0xffffffffu);
         const bool shadow = valid && key_vertex(e.x) >= (uint32_t)P.n;
@@ -522,9 +545,12 @@ struct Worker {
         }
         stat(kStChunks, (unsigned long long)__popc(__ballot_sync(kFull, leader)));
         __syncwarp();
-        // written below the window (work done out of order produced smaller
-        // distances): pull the window back so readers see these buckets first
+        // written below the window: work held in the local queues (L0/L1),
+        // which the window does not see, has smaller distances than the L2
+        // front; pull the window back so readers see these buckets first
         if (lane == 0 && below < W) atomicMin(&P.ctrl->window, (unsigned long long)below);
+        stat(kStPullBack, below < W ? 1u : 0u);
+        stat(kStLowWrite, (unsigned long long)__popc(__ballot_sync(kFull, valid && ab < 2u)));
         stat(kCyL2Write, (unsigned long long)(clock64() - cw0));
         return total;
     }
@@ -533,13 +559,14 @@ struct Worker {
     // looks at absolute bucket W + round * (32 / S) + i / S, shard
     // (home + i) % S.  When the lowest buckets are empty the window moves up
     // to the lowest non-empty one ("base is increased by delta when the first
-    // bucket is empty", Section 4.2); the skipped buckets are probed again
-    // after the move and the window goes back if one of them was written in
-    // the meantime (writers below the window also pull it back), so no work
-    // is left behind it.  Claims up to `want` chunks of the lowest non-empty
-    // ring among the first bnum buckets with one CAS on its read ticket.
-    // Returns the number of chunks claimed (warp-uniform) with their ring and
-    // first ticket.
+    // bucket is empty", Section 4.2).  The window only moves forward: ring k
+    // serves buckets k, k + bmax, ..., so moving it back would let elements
+    // written to the far end of the window pass for the lowest buckets.
+    // Writers keep every element inside the window (clamp_bucket), and every
+    // ring lies inside it, so no element is left behind.  Claims up to `want`
+    // chunks of the lowest non-empty ring among the first bnum buckets with
+    // one CAS on its read ticket.  Returns the number of chunks claimed
+    // (warp-uniform) with their ring and first ticket.
     __device__ uint32_t l2_claim(uint32_t want, uint32_t& ring_out, uint32_t& t_out) {
         unsigned long long win = 0;
         if (lane == 0) win = window();
@@ -561,29 +588,8 @@ struct Worker {
             if (nonempty == 0) continue;
             const int first = __ffs(nonempty) - 1;
             const uint32_t first_rel = r0 + (uint32_t)first / S_;
-            if (first_rel > 0) {
-                int moved = 0;
-                if (lane == 0) moved = atomicCAS(&P.ctrl->window, win, (unsigned long long)(W + first_rel)) == win;
-                moved = __shfl_sync(kFull, moved, 0);
-                if (moved) {
-                    // re-probe the skipped buckets (all shards): a writer may have
-                    // published there between the probe and the move
-                    for (uint32_t q0 = 0; q0 < first_rel * S_; q0 += 32) {
-                        const uint32_t qi = q0 + lane;
-                        const bool pr = qi < first_rel * S_;
-                        const uint32_t qring = ((W + qi / S_) % (uint32_t)P.bmax) * S_ + (qi & (S_ - 1u));
-                        bool back = false;
-                        if (pr) back = ahead(ld_relaxed(P.l2.wt + (size_t)qring * 32),
-                                             ld_relaxed(P.l2.rt + (size_t)qring * 32));
-                        const uint32_t bm = __ballot_sync(kFull, back);
-                        if (bm) {
-                            if (lane == 0)
-                                atomicMin(&P.ctrl->window, (unsigned long long)(W + (q0 + __ffs(bm) - 1) / S_));
-                            break;
-                        }
-                    }
-                }
-            }
+            if (first_rel > 0 && lane == 0)
+                if (atomicCAS(&P.ctrl->window, win, (unsigned long long)(W + first_rel)) == win) sst()[kStAdvance]++;
             // candidates: non-empty rings of buckets within bnum of the first one
             uint32_t cand = __ballot_sync(kFull, ne && rel < first_rel + (uint32_t)P.bnum);
             while (cand) {
@@ -1157,9 +1163,20 @@ struct Worker {
         return ab;
     }
 
+    // The bucket an element is written to.  Ring k serves buckets k, k + bmax,
+    // ...; elements beyond the window's reach go to bucket W + reach - 1 with
+    // reach = bmax - kWindowGuard, so that after the window is pulled back by
+    // up to kWindowGuard buckets no ring holds elements of two buckets of the
+    // window.  Elements below W keep their bucket (the writer pulls W back).
+    __device__ __forceinline__ uint32_t clamp_bucket(uint32_t ab, uint32_t W) const {
+        const uint32_t reach = (uint32_t)P.bmax > 2u * kWindowGuard ? (uint32_t)P.bmax - kWindowGuard
+                                                                  : (uint32_t)P.bmax;
+        if (ab > W && ab - W >= reach) return W + reach - 1u;
+        return ab;
+    }
+
     __device__ __forceinline__ uint32_t ring_bucket(uint32_t key, uint32_t d, uint32_t W, uint32_t& ab) const {
-        ab = abs_bucket(key, d);
-        if (ab > W && ab - W >= (uint32_t)P.bmax) ab = W + (uint32_t)P.bmax - 1u;
+        ab = clamp_bucket(abs_bucket(key, d), W);
         return ab % (uint32_t)P.bmax;
     }
 
@@ -1333,10 +1350,16 @@ struct Worker {
     // route the improved elements of one round: writes through light arcs
     // (w <= near_w, the light/heavy split of delta-stepping) go to L0, the
     // others to the far staging and then their L2 bucket
-    __device__ __forceinline__ void push_round(bool imp, uint32_t key, uint32_t nd, uint32_t w) {
+    // `front` bounds what stays local: a light-arc write whose distance is
+    // beyond the window front (W + F) * delta belongs to a later bucket and
+    // goes to L2 like a heavy one (delta-stepping relaxes light arcs within
+    // the current bucket only).  With admission offsets (serving) front is a
+    // bucket, otherwise a distance.
+    __device__ __forceinline__ void push_round(bool imp, uint32_t key, uint32_t nd, uint32_t w, uint32_t front) {
         // a shadow vertex (a slice of a hub's arcs) always goes to L2 so that
         // the slices of one hub spread over all blocks
-        const bool nearv = imp && w <= P.near_w && key_vertex(key) < (uint32_t)P.n;
+        const bool inside = MQ && P.qoff ? abs_bucket(key, nd) <= front : nd <= front;
+        const bool nearv = imp && w <= P.near_w && inside && key_vertex(key) < (uint32_t)P.n;
         const uint32_t m = __ballot_sync(kFull, nearv);
         if (m) {
             if (nearv) scratch()[__popc(m & lanemask_lt())] = make_uint2(key, nd);
@@ -1436,6 +1459,15 @@ struct Worker {
         }
         const int32_t total = __shfl_sync(kFull, incl, 31);
         const uint32_t myq = MQ ? key_query(key) : 0u;
+        // the window front for this batch (see push_round); no bound when
+        // every write is local (near_deltas = 0, as in Listing 1)
+        uint32_t front = kInfU32;
+        if (SSSP_FRONT_BOUND && P.near_w != kInfU32) {
+            unsigned long long win = 0;
+            if (lane == 0) win = window();
+            const uint32_t W = (uint32_t)__shfl_sync(kFull, win, 0);
+            front = MQ && P.qoff ? W + (uint32_t)P.filter_deltas : A::upper(W, P.delta, P.filter_deltas);
+        }
         // predecessor id: a shadow vertex stands for its owner
         uint32_t pu = 0;
         if (PRED != 0 && valid) {
@@ -1448,6 +1480,11 @@ struct Worker {
             const int32_t shs = __reduce_add_sync(kFull, (uint32_t)sh);
             if (shs) stat(kStRelaxShadow, (unsigned long long)shs);
         }
+#if SSSP_PIPELINE
+        // software pipeline: round r + 1's adjacency load is issued before
+        // round r's distance load and update
+        RoundIn nx = round_in(0, total, ex, rs, du, myq, pu);
+#endif
         for (int32_t g0 = 0; g0 < total; g0 += 32) {
             if (g0 && (g0 & 4095) == 0) {
                 int stop = 0;
@@ -1455,14 +1492,19 @@ struct Worker {
                 if (__shfl_sync(kFull, stop, 0)) break;
             }
             stat(kStRounds, 1);
+#if SSSP_PIPELINE
+            const RoundIn cu = nx;
+            if (g0 + 32 < total) nx = round_in(g0 + 32, total, ex, rs, du, myq, pu);
+#else
             const RoundIn cu = round_in(g0, total, ex, rs, du, myq, pu);
+#endif
             uint32_t nd = 0;
             bool imp = false;
             if (cu.in) {
                 const size_t vidx = MQ ? (size_t)cu.q * (size_t)P.nv + cu.a.x : (size_t)cu.a.x;
                 imp = relax_cur(vidx, cu.pu, cu.du, cu.a.y, ld_dist(dist() + vidx), nd);
             }
-            push_round(imp, MQ ? ((cu.q << P.vbits) | cu.a.x) : cu.a.x, nd, cu.a.y);
+            push_round(imp, MQ ? ((cu.q << P.vbits) | cu.a.x) : cu.a.x, nd, cu.a.y, front);
         }
         return consumed;
     }
@@ -1474,6 +1516,21 @@ struct Worker {
         }
     }
 
+    // ---- run-time sampling ----------------------------------------------------
+    __device__ __noinline__ void sample() {
+        const unsigned long long now = gtime();
+        BlockShared* B = S();
+        if (now < B->next_sample || B->nsamples >= (uint32_t)P.timeline_cap) return;
+        B->next_sample = now + P.timeline_ns;
+        unsigned long long* o = P.timeline + (size_t)B->nsamples * kTimelineFields;
+        o[0] = now - B->t0;
+        o[1] = ld_acquire64(&P.ctrl->reserve);
+        o[2] = ld_acquire64(&P.ctrl->done);
+        o[3] = ld_acquire64(&P.ctrl->window);
+        o[4] = *(volatile uint32_t*)&B->busy;
+        B->nsamples++;
+    }
+
     // ---- the worker loop (Listing 2, work_kernel) ---------------------------
     __device__ void run() {
         uint32_t idle_ns = 0;
@@ -1481,6 +1538,7 @@ struct Worker {
         for (;;) {
             mark(1, iter);
             stat(kStIter, 1);
+            if (P.timeline && blockIdx.x == 0 && threadIdx.x == 0) sample();
             if ((++iter & 7u) == 0 || idle_ns || P.slice_ns) {
                 int stop = 0;
                 if (lane == 0) {
@@ -1543,7 +1601,9 @@ struct Worker {
             }
             idle_ns = 0;
             mark(7, iter);
+            if (P.timeline && blockIdx.x == 0 && lane == 0) atomicAdd(&S()->busy, 1u);
             dec += relax_batch(valid, e);
+            if (P.timeline && blockIdx.x == 0 && lane == 0) atomicSub(&S()->busy, 1u);
             stat(kCyRelax, (unsigned long long)((unsigned long long)(clock64() - c3)));
             mark(10, iter);
             acct_apply();
@@ -1642,6 +1702,10 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
         unsigned long long win = ld_acquire64(&P.ctrl->window);
         S->nf = Arith<WT>::upper((uint32_t)win, P.delta, 1.0f);
         S->deadline = gtime() + P.timeout_ns;
+        S->t0 = gtime();
+        S->next_sample = 0;
+        S->nsamples = 0;
+        S->busy = 0;
         S->slice_end = ~0ull;
         if (P.slice_ns) {
             // the first block to start fixes the slice's end for all blocks

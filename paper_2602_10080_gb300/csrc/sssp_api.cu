@@ -610,6 +610,16 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
                 (uint32_t*)work, cells, g->wtype == SSSP_W_F32 ? kInfF32 : kInfU32);
         seed_kernel<<<1, 32, 0, stream>>>(P, srcs_d, src0, nq, pred_mode ? 1 : 0);
         cudaEventRecord(ws.ev1, stream);
+        // SSSP_DEBUG >= 4: run-time sampling into mapped host memory, printed after the solve
+        unsigned long long* tl_h = nullptr;
+        const int tl_cap = 4096;
+        if (dbg > 3 && cudaHostAlloc((void**)&tl_h, (size_t)tl_cap * kTimelineFields * 8, cudaHostAllocMapped) ==
+                           cudaSuccess) {
+            std::memset(tl_h, 0xff, (size_t)tl_cap * kTimelineFields * 8);
+            cudaHostGetDevicePointer((void**)&P.timeline, tl_h, 0);
+            P.timeline_cap = tl_cap;
+            P.timeline_ns = 20000;
+        }
         unsigned long long* trace_h = nullptr;
         const size_t nthreads_total = (size_t)grid * threads;
         if (dbg > 2 && cudaHostAlloc((void**)&trace_h, nthreads_total * 8, cudaHostAllocMapped) == cudaSuccess) {
@@ -685,6 +695,15 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
             if (dbg) std::fprintf(stderr, "[sssp] stream error: %s\n", cudaGetErrorString(ce));
             return cuda_status(ce);
         }
+        if (tl_h) {
+            std::fprintf(stderr, "[sssp] timeline (us, L2 written, L2 done, window, busy warps of block 0):\n");
+            for (int i = 0; i < tl_cap && tl_h[(size_t)i * kTimelineFields] != ~0ull; i++) {
+                const unsigned long long* o = tl_h + (size_t)i * kTimelineFields;
+                std::fprintf(stderr, "[sssp]   %8.1f %12llu %12llu %8llu %3llu\n", o[0] / 1000.0, o[1], o[2], o[3],
+                             o[4]);
+            }
+            cudaFreeHost(tl_h);
+        }
         const Ctrl& hc = *ws.host_ctrl;
         float ms_kernel = 0, ms_total = 0;
         cudaEventElapsedTime(&ms_kernel, ws.ev1, ws.ev2);
@@ -728,6 +747,9 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
                          hc.stats[kStRefill], hc.stats[kStLockSpin], hc.stats[kStWaitSpin], hc.stats[kCyRelax],
                          hc.stats[kCyL1], hc.stats[kCyL2Write], hc.stats[kCyGlobalRead], hc.stats[kCyIdle],
                          hc.stats[kCyL0]);
+        if (dbg > 1)
+            std::fprintf(stderr, "[sssp]   window pull-backs %llu advances %llu elements written to buckets 0-1 %llu\n",
+                         hc.stats[kStPullBack], hc.stats[kStAdvance], hc.stats[kStLowWrite]);
         if (hc.error == kErrNone && hc.finished) return SSSP_OK;
         if (dbg)
             std::fprintf(stderr, "[sssp] solve failed: error=%d where=%d info=%d finished=%d reserve=%llu done=%llu "
