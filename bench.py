@@ -246,6 +246,37 @@ def batch_leg(S, gg, torch, wtype: str = "u32", nq: int = 256, seq_sample: int =
         G.close()
 
 
+def road_leg(S, gg, torch, nsrc: int = 4, tune_ms: int = 3000):
+    """Road-shaped high-diameter graph (4096^2 grid, 5% of edges dropped,
+    0.5% long-range edges): the prior configuration against the autotuned
+    one on the same sources (distances and predecessors)."""
+    g = gg.workload("road4096")
+    srcs, _ = gg.giant_sources(g, 16, seed=2)
+    G = S.Graph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda(),
+                torch.from_numpy(g.w_bits.view(np.int32)).cuda(), g.wtype)
+    try:
+        d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        p = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        row_ptr_t = torch.from_numpy(g.row_ptr).cuda()
+        prior = S.sssp_autotune(G.handle, None, 0)
+        tuned = G.autotune(torch.from_numpy(srcs[:2].astype(np.int32)).cuda(), tune_ms)
+        out = {"workload": f"road4096 (n={g.n}, m={g.m}), {nsrc} giant-component sources"}
+        for name, cfg in (("prior", prior), ("autotuned", tuned)):
+            G.solve(int(srcs[0]), d, p, cfg)
+            ms, arcs = [], 0
+            for s in srcs[2:2 + nsrc]:
+                G.solve(int(s), d, p, cfg)
+                ms.append(S.sssp_last_stats(G.handle).kernel_ms)
+                arcs += reached(row_ptr_t, d, g.wtype)[0]
+            out[name] = {"ms_per_solve": round(float(np.mean(ms)), 3),
+                         "gteps": round(arcs / (sum(ms) / 1e3) / 1e9, 3),
+                         "config": {k: v for k, v in cfg.as_dict().items()
+                                    if k in ("l1_type", "delta_u32", "bnum", "near_deltas", "block_threads")}}
+        return out
+    finally:
+        G.close()
+
+
 SERVE_GRAPHS = ("grid1024", "rmat18", "rmat20", "rmat22", "er21")
 
 
@@ -466,6 +497,7 @@ def main():
                                           f"one per thread ({cdt:.1f} s)"}
     if rank == 0 and not args.no_extras:
         line["batch"] = [batch_leg(S, gg, torch, "u32"), batch_leg(S, gg, torch, "f32")]
+        line["road"] = road_leg(S, gg, torch)
         cache = {}
         if args.workload in SERVE_GRAPHS:
             cache[args.workload] = (g, G, gg.giant_sources(g, 4096, seed=2)[0])

@@ -282,7 +282,9 @@ typedef struct sssp_serve_options {
                                   (0 = a quarter of the free device memory at creation) */
     int32_t max_slots;         /* concurrent queries per lane, 1..4096 (default 256); also
                                   bounded by 2^32 / (vertices rounded up to a power of two) */
-    int32_t slice_us;          /* length of one slice, 50..100000 (default 1000) */
+    int32_t slice_us;          /* length of one slice, 50..100000 (default 1000); a lane with
+                                  q queries in flight runs slices of min(8, max(1, q / 4))
+                                  times this */
     int32_t max_queued;        /* queries waiting for a slot; beyond it submit returns
                                   SSSP_E_BUSY (default 65536) */
     int32_t ring_shift;        /* initial L2 ring capacity per lane: (slots x vertices) >>

@@ -64,9 +64,6 @@ constexpr int kStageCap = 64;       // block staging per L2 bucket (elements)
 #define SSSP_FRONT_BOUND 1
 #endif
 constexpr uint32_t kWindowGuard = SSSP_WINDOW_GUARD;  // buckets kept clear at the far end of the L2 window
-#ifndef SSSP_PIPELINE
-#define SSSP_PIPELINE 0
-#endif
 constexpr uint32_t kInfU32 = 0xffffffffu;
 constexpr uint32_t kEmptyKey = 0xffffffffu;  // a free L1 slot (never a valid element key)
 constexpr uint32_t kSatU32 = 0xfffffffeu;
@@ -148,6 +145,7 @@ struct KParams {
     unsigned long long timeout_ns;
     unsigned long long slice_ns;   // serving: end the launch after this long, draining local queues to L2 (0 = run to completion)
     const uint32_t* qoff;          // serving: per-query bucket offset (the window position when the query was admitted), or null
+    int* qlive;                    // serving: per-query count of elements in L2 (writes add, reads subtract), or null
     unsigned long long* trace;   // debug only: per-lane (location << 48 | iteration), mapped host memory
     unsigned long long* timeline; // run-time sampling (or null): kTimelineFields words per sample
     int32_t timeline_cap;         // samples that fit
@@ -458,6 +456,16 @@ struct Worker {
         return (blockIdx.x + (threadIdx.x >> 5)) & (uint32_t)(P.shards - 1);
     }
 
+    // Serving: adds `sign` per valid element to its query's L2 count, one
+    // atomic per distinct query of the warp.  At the end of a slice every
+    // element is in L2, so a count of zero means the query is complete.
+    __device__ __forceinline__ void count_live(bool valid, uint32_t key, int sign) {
+        if (!MQ || !P.qlive) return;
+        const uint32_t q = valid ? key_query(key) : 0xffffffffu;
+        const uint32_t grp = __match_any_sync(kFull, q);
+        if (valid && (grp & lanemask_lt()) == 0u) atomicAdd(P.qlive + q, sign * __popc(grp));
+    }
+
     // Writes the valid lanes' elements to the L2 bucket of their distance
     // (this warp's shard of it).  Lanes are grouped per bucket with
     // __match_any_sync and every group fills one chunk with a single ticket
@@ -535,6 +543,7 @@ struct Worker {
         ring = __shfl_sync(kFull, ring, ldr);
         okw = __shfl_sync(kFull, okw, ldr);
         if (!__all_sync(kFull, okw || !valid)) return total;
+        count_live(valid, e.x, 1);
         const size_t slot = (size_t)ring * P.l2.nch + (t & (P.l2.nch - 1u));
         if (valid) P.l2.data[slot * kChunk + __popc(grp & lanemask_lt())] = e;
         __syncwarp();
@@ -651,6 +660,7 @@ struct Worker {
         const size_t slot = (size_t)ring * P.l2.nch + (tj & (P.l2.nch - 1u));
         valid = lane < c;
         if (valid) e = P.l2.data[slot * kChunk + lane];
+        count_live(valid, e.x, -1);
         __syncwarp();
         if (lane == 0) {
             __threadfence();
@@ -1480,11 +1490,6 @@ struct Worker {
             const int32_t shs = __reduce_add_sync(kFull, (uint32_t)sh);
             if (shs) stat(kStRelaxShadow, (unsigned long long)shs);
         }
-#if SSSP_PIPELINE
-        // software pipeline: round r + 1's adjacency load is issued before
-        // round r's distance load and update
-        RoundIn nx = round_in(0, total, ex, rs, du, myq, pu);
-#endif
         for (int32_t g0 = 0; g0 < total; g0 += 32) {
             if (g0 && (g0 & 4095) == 0) {
                 int stop = 0;
@@ -1492,12 +1497,7 @@ struct Worker {
                 if (__shfl_sync(kFull, stop, 0)) break;
             }
             stat(kStRounds, 1);
-#if SSSP_PIPELINE
-            const RoundIn cu = nx;
-            if (g0 + 32 < total) nx = round_in(g0 + 32, total, ex, rs, du, myq, pu);
-#else
             const RoundIn cu = round_in(g0, total, ex, rs, du, myq, pu);
-#endif
             uint32_t nd = 0;
             bool imp = false;
             if (cu.in) {

@@ -19,7 +19,7 @@
 //      work already in flight (bucket = floor(d / delta) + offset);
 //   4. grows the rings (migrating the live chunks) when one is half full.
 // Lanes of different graphs run concurrently on their own streams and
-// split the SMs between them.
+// share the SMs in proportion to their queries in flight.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -103,6 +103,7 @@ __global__ void serve_seed_kernel(KParams P, const int2* adm, int32_t nadm, uint
             else
                 reinterpret_cast<uint32_t*>(P.dist)[di] = 0u;
             qoff[q.x] = W;
+            if (P.qlive) P.qlive[q.x] = 1;   // the source, in L2
         }
         __syncwarp();
         if (lane == 0) {
@@ -116,72 +117,23 @@ __global__ void serve_seed_kernel(KParams P, const int2* adm, int32_t nadm, uint
     __threadfence();
 }
 
-// Counts the L2 elements of every slot (live[slot]) and the fullest ring's
-// chunk count (occ[0]).  Runs between slices, when every chunk in [rt, wt)
-// of a ring is full.  Every block prefix-sums the rings' chunk counts in
-// shared memory; the warps of the grid then take the concatenated chunks
-// in turn, so one very full ring does not serialise the scan.
-constexpr int kScanMaxRings = 1024;
-__global__ void serve_scan_kernel(Rings R, uint32_t nrings, int32_t vbits, uint32_t cap, uint32_t* live,
-                                  uint32_t* occ) {
-    __shared__ uint32_t pre[kScanMaxRings + 1];
-    __shared__ uint32_t rbase[kScanMaxRings];
+// The fullest ring's chunk count (occ[0]) and all rings' (occ[1]), between
+// slices.  One block.
+__global__ void serve_occ_kernel(Rings R, uint32_t nrings, uint32_t* occ) {
+    uint32_t mx = 0, sum = 0;
     for (uint32_t k = threadIdx.x; k < nrings; k += blockDim.x) {
-        const uint32_t r = R.rt[(size_t)k * 32], w = R.wt[(size_t)k * 32];
-        rbase[k] = r;
-        pre[k] = w - r;
-        if (blockIdx.x == 0 && w != r) atomicMax(occ, w - r);
+        const uint32_t c = R.wt[(size_t)k * 32] - R.rt[(size_t)k * 32];
+        mx = max(mx, c);
+        sum += c;
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        // exclusive prefix sum: lane i owns a contiguous segment of the rings
-        const uint32_t l = threadIdx.x, per = (nrings + 31u) / 32u;
-        const uint32_t b = min(l * per, nrings), e = min(b + per, nrings);
-        uint32_t sum = 0;
-        for (uint32_t k = b; k < e; k++) sum += pre[k];
-        uint32_t incl = sum;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t x = __shfl_up_sync(kFull, incl, o);
-            if (l >= (uint32_t)o) incl += x;
-        }
-        uint32_t acc = incl - sum;
-        for (uint32_t k = b; k < e; k++) {
-            const uint32_t c = pre[k];
-            pre[k] = acc;
-            acc += c;
-        }
-        if (l == 31) {
-            pre[nrings] = incl;
-            if (blockIdx.x == 0) occ[1] = incl;
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+        sum += __shfl_xor_sync(kFull, sum, o);
     }
-    __syncthreads();
-    const uint32_t total = pre[nrings];
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    // per-block counts in shared memory, one global add per slot at the end
-    extern __shared__ uint32_t hist[];
-    for (uint32_t k = threadIdx.x; k < cap; k += blockDim.x) hist[k] = 0;
-    __syncthreads();
-    for (uint32_t c = gw; c < total; c += nwarps) {
-        // ring: the last k with pre[k] <= c
-        uint32_t lo = 0, hi = nrings;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (pre[mid] <= c) lo = mid;
-            else hi = mid;
-        }
-        const size_t slot = (size_t)lo * R.nch + ((rbase[lo] + (c - pre[lo])) & (R.nch - 1u));
-        const uint32_t n = R.cnt[slot];
-        if (lane < n) {
-            const uint32_t q = R.data[slot * kChunk + lane].x >> vbits;
-            if (q < cap) atomicAdd(hist + q, 1u);
-        }
+    if ((threadIdx.x & 31u) == 0) {
+        atomicMax(occ, mx);
+        atomicAdd(occ + 1, sum);
     }
-    __syncthreads();
-    for (uint32_t k = threadIdx.x; k < cap; k += blockDim.x)
-        if (hist[k]) atomicAdd(live + k, hist[k]);
 }
 
 // Copies every ring's live chunks [rt, wt) to the front of the matching
@@ -439,6 +391,7 @@ int lane_rings_fresh(sssp_server* s, Lane* L, uint32_t nch) {
     ring_carve(L->ring_mem, nrings, nch, lane_margin(L), &L->rings);
     serve_reset_kernel<<<blocks_for((size_t)nrings * nch, s->sms), 256, 0, L->stream>>>(L->rings, nrings,
                                                                                      L->ctrl);
+    if (L->live) cudaMemsetAsync(L->live, 0, ((size_t)L->cap + 2) * 4, L->stream);  // the rings are empty
     return cuda_status(cudaGetLastError());
 }
 
@@ -511,7 +464,9 @@ int lane_grow_slots(sssp_server* s, Lane* L, uint32_t want) {
         cudaFree(adm);
         return SSSP_E_NOMEM;
     }
+    cudaMemsetAsync(live, 0, ((size_t)ncap + 2) * 4, L->stream);
     if (L->cap) {
+        cudaMemcpyAsync(live, L->live, (size_t)L->cap * 4, cudaMemcpyDeviceToDevice, L->stream);
         cudaMemcpyAsync(work, L->work, (size_t)L->cap * nv * L->cell, cudaMemcpyDeviceToDevice, L->stream);
         cudaMemcpyAsync(qoff, L->qoff, (size_t)L->cap * 4, cudaMemcpyDeviceToDevice, L->stream);
         // admissions already staged for the coming slice
@@ -724,9 +679,9 @@ void admit(sssp_server* s) {
 
 // Launches one slice on every lane that has work and no slice in flight.
 int launch_ready(sssp_server* s) {
-    int nact = 0;
-    for (Lane* L : s->lanes)
-        if (L->running + L->draining > 0) nact++;
+    // the SMs are shared in proportion to each lane's queries in flight
+    int total = 0;
+    for (Lane* L : s->lanes) total += L->running + L->draining;
     for (Lane* L : s->lanes) {
         if (L->inflight || L->running + L->draining == 0) continue;
         KParams P = L->plan.P;
@@ -736,8 +691,12 @@ int launch_ready(sssp_server* s) {
         P.vmask = (1u << L->vbits) - 1u;
         P.l2 = L->rings;
         P.ctrl = L->ctrl;
-        P.slice_ns = (unsigned long long)s->opt.slice_us * 1000ull;
+        // a busy lane runs longer slices (fewer drains and restarts); with
+        // many queries in flight, one of them finishes every few ms anyway
+        const int scale = std::min(8, std::max(1, (L->running + L->draining) / 4));
+        P.slice_ns = (unsigned long long)s->opt.slice_us * 1000ull * (unsigned long long)scale;
         P.qoff = L->qoff;
+        P.qlive = reinterpret_cast<int*>(L->live);
         // a warp's batch stays short, so a slice ends close to its deadline
         P.max_arcs = std::min(P.max_arcs, 1024);
         const bool packed = L->pred_mode != 0;
@@ -748,15 +707,15 @@ int launch_ready(sssp_server* s) {
         }
         serve_seed_kernel<<<1, 32, 0, L->stream>>>(P, L->adm, L->nadm, L->qoff, packed);
         L->nadm = 0;
-        // the SMs are split evenly between the lanes with work
-        const int grid = std::max(8, L->plan.grid / std::max(1, nact));
+        const int share = (int)((long long)L->plan.grid * (L->running + L->draining) / std::max(1, total));
+        const int grid = std::max(std::max(8, s->sms / 8), std::min(L->plan.grid, share));
         cudaEventRecord(L->k0, L->stream);
         cudaError_t e = launch_mlmq(L->plan.key, dim3(grid), dim3(L->plan.threads), L->plan.smem, L->stream, P);
         if (e != cudaSuccess) return cuda_status(e);
         cudaEventRecord(L->k1, L->stream);
-        cudaMemsetAsync(L->live, 0, ((size_t)L->cap + 2) * 4, L->stream);
-        serve_scan_kernel<<<s->sms * 4, 256, (size_t)L->cap * 4, L->stream>>>(L->rings, L->nrings, L->vbits,
-                                                                             L->cap, L->live, L->live + L->cap);
+        // per-slot L2 counts are kept by the kernel; [cap], [cap + 1]: ring occupancy
+        cudaMemsetAsync(L->live + L->cap, 0, 2 * 4, L->stream);
+        serve_occ_kernel<<<1, 256, 0, L->stream>>>(L->rings, L->nrings, L->live + L->cap);
         cudaMemcpyAsync(L->live_h, L->live, ((size_t)L->cap + 2) * 4, cudaMemcpyDeviceToHost, L->stream);
         cudaEventRecord(L->k2, L->stream);
         cudaMemcpyAsync(L->ctrl_h, L->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, L->stream);
@@ -830,7 +789,7 @@ int collect_lane(sssp_server* s, Lane* L) {
             float sm = 0;
             if (cudaEventElapsedTime(&sm, L->k1, L->k2) == cudaSuccess) L->dbg_scan_ms += sm;
             L->dbg_chunks += L->live_h[L->cap + 1];
-            for (uint32_t k = 0; k < L->cap; k++) L->dbg_elems += L->live_h[k];
+            for (uint32_t k = 0; k < L->cap; k++) L->dbg_elems += (int32_t)L->live_h[k];
         }
     }
     const Clock::time_point now = Clock::now();
