@@ -277,6 +277,43 @@ def road_leg(S, gg, torch, nsrc: int = 4, tune_ms: int = 3000):
         G.close()
 
 
+def queues_leg(S, gg, torch, nsrc: int = 4):
+    """The paper's comparison of the multi-level queue with single-queue
+    designs, on this GPU: the prior MLMQ configuration against every write
+    going straight to a delta-bucketed L2 (L2DQ only) or to one FIFO."""
+    out = {}
+    for name in ("rmat20", "grid1024"):
+        g = gg.workload(name)
+        srcs, _ = gg.giant_sources(g, 8, seed=2)
+        G = S.Graph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda(),
+                    torch.from_numpy(g.w_bits.view(np.int32)).cuda(), g.wtype)
+        try:
+            d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+            prior = S.sssp_autotune(G.handle, None, 0)
+            variants = {"mlmq": prior}
+            for vname, l2 in (("l2dq_only", S.L2_BUCKET), ("fifo_only", S.L2_VECTOR)):
+                c = S.sssp_autotune(G.handle, None, 0)
+                c.l2_only, c.l2_type = 1, l2
+                if l2 == S.L2_VECTOR:
+                    c.bmax = c.bnum = 1
+                variants[vname] = c
+            res = {}
+            for vname, c in variants.items():
+                G.solve(int(srcs[0]), d, None, c)
+                ms, rl = [], []
+                for s in srcs[1:1 + nsrc]:
+                    G.solve(int(s), d, None, c)
+                    st = S.sssp_last_stats(G.handle)
+                    ms.append(st.kernel_ms)
+                    rl.append(st.relax_arcs)
+                res[vname] = {"ms_per_solve": round(float(np.mean(ms)), 3),
+                              "relaxed_arcs": int(np.mean(rl))}
+            out[name] = res
+        finally:
+            G.close()
+    return out
+
+
 SERVE_GRAPHS = ("grid1024", "rmat18", "rmat20", "rmat22", "er21")
 
 
@@ -498,6 +535,7 @@ def main():
     if rank == 0 and not args.no_extras:
         line["batch"] = [batch_leg(S, gg, torch, "u32"), batch_leg(S, gg, torch, "f32")]
         line["road"] = road_leg(S, gg, torch)
+        line["queues"] = queues_leg(S, gg, torch)
         cache = {}
         if args.workload in SERVE_GRAPHS:
             cache[args.workload] = (g, G, gg.giant_sources(g, 4096, seed=2)[0])

@@ -120,7 +120,11 @@ typedef struct sssp_config {
     int32_t block_threads; /* threads per block: 256, 512 or 1024 */
     int32_t blocks_per_sm; /* resident blocks per SM (0 = as many as fit) */
     int32_t timeout_ms;    /* device watchdog for one solve (0 = library default, 20 s) */
-    int32_t reserved[3];   /* must be zero */
+    int32_t l2_only;       /* 1 = single-queue baseline: every write goes straight to L2 (no
+                              L0/L1, no block staging, one chunk per read); with l2_type
+                              SSSP_L2_BUCKET this is a delta-stepping (L2DQ-only) queue, with
+                              SSSP_L2_VECTOR a single FIFO (Section 2.2's single-queue designs) */
+    int32_t reserved[2];   /* must be zero */
 } sssp_config;
 
 /* Graph features of Table 2 (Section 3.5), computed at creation. */

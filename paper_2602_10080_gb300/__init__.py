@@ -47,7 +47,7 @@ class sssp_config(ctypes.Structure):
         ("filter_deltas", ctypes.c_float), ("near_deltas", ctypes.c_float), ("max_arcs", ctypes.c_int32),
         ("claim", ctypes.c_int32), ("shards", ctypes.c_int32), ("refillers", ctypes.c_int32),
         ("stage", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-        ("timeout_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+        ("timeout_ms", ctypes.c_int32), ("l2_only", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
     ]
 
     def as_dict(self) -> dict:

@@ -141,6 +141,7 @@ struct KParams {
     int32_t claim;           // chunks per L2 claim (1..kMaxClaim)
     int32_t refillers;       // warps of a block that may refill L1 from L2 at the same time
     int32_t stage;           // 1: heavy-arc writes are pooled per bucket in the block before L2
+    int32_t l2_only;         // 1: single-queue baseline (every write to L2, one chunk per read)
     int32_t scratch_off, far_off, stat_off, stage_off, l1_off;  // byte offsets in dynamic shared memory
     unsigned long long timeout_ns;
     unsigned long long slice_ns;   // serving: end the launch after this long, draining local queues to L2 (0 = run to completion)
@@ -1120,6 +1121,12 @@ struct Worker {
             e[r] = l0[r];
         }
         l0h = l0t = 0;
+        if (P.l2_only) {
+            // single-queue baseline: no L1, the elements go to L2
+#pragma unroll
+            for (int r = 0; r < R; r++) dec += l2_write(v[r], e[r]);
+            return;
+        }
         // the elements become visible: count every private push now (the
         // far-staged ones too -- counting early only delays the block's
         // done flush, counting late could end the solve too soon)
@@ -1369,7 +1376,7 @@ struct Worker {
         // a shadow vertex (a slice of a hub's arcs) always goes to L2 so that
         // the slices of one hub spread over all blocks
         const bool inside = MQ && P.qoff ? abs_bucket(key, nd) <= front : nd <= front;
-        const bool nearv = imp && w <= P.near_w && inside && key_vertex(key) < (uint32_t)P.n;
+        const bool nearv = imp && !P.l2_only && w <= P.near_w && inside && key_vertex(key) < (uint32_t)P.n;
         const uint32_t m = __ballot_sync(kFull, nearv);
         if (m) {
             if (nearv) scratch()[__popc(m & lanemask_lt())] = make_uint2(key, nd);

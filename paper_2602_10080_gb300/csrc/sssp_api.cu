@@ -451,7 +451,8 @@ int validate_config(const sssp_config* c) {
     if (c->block_threads != 256 && c->block_threads != 512 && c->block_threads != 1024) return SSSP_E_INVAL;
     if (c->blocks_per_sm < 0 || c->blocks_per_sm > 8 || c->timeout_ms < 0) return SSSP_E_INVAL;
     if (c->stage < 0 || c->stage > 1) return SSSP_E_INVAL;
-    for (int i = 0; i < 3; i++)
+    if (c->l2_only < 0 || c->l2_only > 1) return SSSP_E_INVAL;
+    for (int i = 0; i < 2; i++)
         if (c->reserved[i] != 0) return SSSP_E_INVAL;
     return SSSP_OK;
 }
@@ -515,7 +516,9 @@ int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, 
     P.far_off = (int32_t)far_off;
     P.stat_off = (int32_t)stat_off;
     P.stage_off = (int32_t)stage_off;
-    P.stage = cfg.stage ? 1 : 0;
+    P.l2_only = cfg.l2_only ? 1 : 0;
+    P.stage = cfg.stage && !cfg.l2_only ? 1 : 0;
+    if (cfg.l2_only) P.claim = 1;
     P.l1_off = (int32_t)l1_off;
     const int tmo = cfg.timeout_ms > 0 ? cfg.timeout_ms : 20000;
     P.timeout_ns = (unsigned long long)tmo * 1000000ull;

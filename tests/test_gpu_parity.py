@@ -212,3 +212,18 @@ def test_autotune_prior_and_search():
     assert_exact(g, s, d, p)
     d, p = gpu_solve(G, s, pred=True, config=tuned)
     assert_exact(g, s, d, p)
+
+
+@pytest.mark.parametrize("l2", [S.L2_BUCKET, S.L2_VECTOR])
+def test_single_queue_baselines(l2):
+    """The single-queue baselines (every write straight to L2: a bucketed
+    delta-stepping queue, or one FIFO) give the same exact results."""
+    for g, src in ((gg.workload("grid256"), 0), (gg.rmat(14, 16, lo=1, hi=255, seed=3), None),
+                   (gg.random_directed(3000, 20000, 0, 50, seed=9), 5)):
+        G = upload(g)
+        if src is None:
+            src = int(gg.giant_sources(g, 1)[0][0])
+        c = cfg(l2_only=1, l2_type=l2)
+        d, p = gpu_solve(G, src, config=c)
+        assert_exact(g, src, d, p)
+        G.close()
