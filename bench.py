@@ -246,6 +246,22 @@ def batch_leg(S, gg, torch, wtype: str = "u32", nq: int = 256, seq_sample: int =
         G.close()
 
 
+def bfs_leg(S, G, g, srcs, torch, nsrc: int = 4):
+    """Breadth-first search on the same engine (every arc counts 1), on the
+    benchmark graph: levels and parents from `nsrc` of its sources."""
+    lev = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    par = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    row_ptr_t = torch.from_numpy(g.row_ptr).cuda()
+    G.bfs(int(srcs[0]), lev, par)
+    ms, arcs = [], 0
+    for s in srcs[1:1 + nsrc]:
+        G.bfs(int(s), lev, par)
+        ms.append(S.sssp_last_stats(G.handle).kernel_ms)
+        arcs += reached(row_ptr_t, lev, "u32")[0]
+    return {"workload": f"BFS on the benchmark graph, {nsrc} sources", "ms_per_bfs": round(float(np.mean(ms)), 3),
+            "gteps": round(arcs / (sum(ms) / 1e3) / 1e9, 3)}
+
+
 def road_leg(S, gg, torch, nsrc: int = 4, tune_ms: int = 3000):
     """Road-shaped high-diameter graph (4096^2 grid, 5% of edges dropped,
     0.5% long-range edges): the prior configuration against the autotuned
@@ -534,6 +550,7 @@ def main():
                                           f"one per thread ({cdt:.1f} s)"}
     if rank == 0 and not args.no_extras:
         line["batch"] = [batch_leg(S, gg, torch, "u32"), batch_leg(S, gg, torch, "f32")]
+        line["bfs"] = bfs_leg(S, G, g, srcs_all, torch)
         line["road"] = road_leg(S, gg, torch)
         line["queues"] = queues_leg(S, gg, torch)
         cache = {}

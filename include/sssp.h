@@ -266,6 +266,37 @@ SSSP_API int sssp_solve_noalloc(const int32_t *row_ptr, const uint32_t *arcs, in
                                 int32_t wtype, int32_t src, void *dist_out, int32_t *pred_out,
                                 void *stream);
 
+/* Run-time behaviour of one solve (Section 5.3 follows active warps and
+ * processed vertices over time): sssp_solve plus a timeline sampled every
+ * period_us by one lane of block 0 while the kernel runs.
+ *   samples_out  host memory, cap * 6 uint64 words; sample i holds
+ *                [ns since launch, elements written to L2, L2 elements
+ *                completed (published per block, so it lags), elements taken
+ *                for relaxation, the L2 window W (lowest bucket with work),
+ *                warps of block 0 holding a batch].
+ *   *n_out       samples taken (<= cap).
+ * Sampling adds a few atomics per batch; distances and predecessors are
+ * those of sssp_solve.  SSSP_E_INVAL for cap < 1, period_us < 1 or a device
+ * samples_out; otherwise as sssp_solve. */
+SSSP_API int sssp_solve_sampled(sssp_graph *g, int32_t src, void *dist_out, int32_t *pred_out,
+                                const sssp_config *cfg, uint64_t *samples_out, int32_t cap,
+                                int32_t period_us, int32_t *n_out);
+
+/* ------------------------------------------------------------------- BFS -- */
+
+/* Breadth-first search on the same engine (the BFS case study of Section
+ * 5.7): every arc counts 1, whatever the graph's weights, so the
+ * multi-level queue orders the search by level.
+ *   level_out  [n] uint32: hops from src, 0xFFFFFFFF when unreachable
+ *              (host or device memory).
+ *   pred_out   [n] int32 or NULL: the smallest-index parent one level up,
+ *              pred[src] = src, -1 when unreachable.
+ *   cfg        NULL = the graph's configuration; delta 0 means 1 (one
+ *              bucket per level).
+ * Errors as for sssp_solve. */
+SSSP_API int sssp_bfs(sssp_graph *g, int32_t src, uint32_t *level_out, int32_t *pred_out,
+                      const sssp_config *cfg, void *stream);
+
 /* ---------------------------------------------------------------- serving -- */
 
 /* Serving with continuous batching.  (An extension: the paper solves one

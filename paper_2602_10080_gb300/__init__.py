@@ -133,6 +133,9 @@ def lib():
         "sssp_graph_features": (ctypes.c_int, [P, ctypes.POINTER(sssp_features)]),
         "sssp_solve": (ctypes.c_int, [P, I32, P, P, ctypes.POINTER(sssp_config), P]),
         "sssp_solve_batch": (ctypes.c_int, [P, P, I32, P, P, ctypes.POINTER(sssp_config), P]),
+        "sssp_bfs": (ctypes.c_int, [P, I32, P, P, ctypes.POINTER(sssp_config), P]),
+        "sssp_solve_sampled": (ctypes.c_int, [P, I32, P, P, ctypes.POINTER(sssp_config), P, I32, I32,
+                                              ctypes.POINTER(I32)]),
         "sssp_last_stats": (ctypes.c_int, [P, ctypes.POINTER(sssp_stats)]),
         "sssp_autotune": (ctypes.c_int, [P, P, I32, I32, ctypes.POINTER(sssp_config)]),
         "sssp_serve_options_default": (ctypes.c_int, [ctypes.POINTER(sssp_serve_options)]),
@@ -240,6 +243,27 @@ def sssp_autotune(h, srcs=None, budget_ms: int = 0) -> sssp_config:
     return c
 
 
+def sssp_bfs(h, src: int, level_out, pred_out=None, cfg=None, stream=None) -> None:
+    """Breadth-first levels (uint32 hops) and smallest-index parents."""
+    _check(lib().sssp_bfs(h, int(src), _ptr(level_out), _ptr(pred_out), None if cfg is None else ctypes.byref(cfg),
+                          _stream_ptr(stream)), "sssp_bfs")
+
+
+SAMPLE_FIELDS = ("ns", "l2_written", "l2_done", "processed", "window", "busy_warps_block0")
+
+
+def sssp_solve_sampled(h, src: int, dist_out, pred_out=None, cfg=None, cap: int = 4096, period_us: int = 20):
+    """sssp_solve plus its run-time timeline: a numpy uint64 array [samples, 6]
+    with the columns of SAMPLE_FIELDS."""
+    import numpy as np
+    out = np.zeros((cap, len(SAMPLE_FIELDS)), np.uint64)
+    n = ctypes.c_int32()
+    _check(lib().sssp_solve_sampled(h, int(src), _ptr(dist_out), _ptr(pred_out),
+                                    None if cfg is None else ctypes.byref(cfg), out.ctypes.data, int(cap),
+                                    int(period_us), ctypes.byref(n)), "sssp_solve_sampled")
+    return out[:n.value]
+
+
 def sssp_solve_noalloc(row_ptr, arcs, n: int, m: int, wtype: int, src: int, dist_out, pred_out=None,
                        stream=None) -> None:
     """Single-source solve with no allocation (all arrays device memory; `arcs`
@@ -338,6 +362,9 @@ class Graph:
 
     def solve(self, src, dist_out, pred_out=None, cfg=None, stream=None):
         sssp_solve(self.handle, src, dist_out, pred_out, cfg, stream)
+
+    def bfs(self, src, level_out, pred_out=None, cfg=None, stream=None):
+        sssp_bfs(self.handle, src, level_out, pred_out, cfg, stream)
 
     def solve_batch(self, srcs, dist_out, pred_out=None, cfg=None, stream=None):
         sssp_solve_batch(self.handle, srcs, dist_out, pred_out, cfg, stream)

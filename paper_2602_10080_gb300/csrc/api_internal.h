@@ -30,6 +30,8 @@ struct Workspace {
     size_t out_p_n = 0;
     int32_t* srcs = nullptr;
     size_t srcs_n = 0;
+    unsigned long long* tl = nullptr;   // run-time sampling buffer
+    size_t tl_n = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
 
     int ensure_queue(uint32_t nrings, uint32_t nch, uint32_t margin, cudaStream_t s, int sms);
@@ -72,13 +74,24 @@ struct LaunchPlan {
 
 int cuda_status(cudaError_t e);
 int pred_mode_for(const Graph* g);
-int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, LaunchPlan* out);
+int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, LaunchPlan* out,
+                bool unit = false);
 bool is_device_ptr(const void* p);
 void resolve_auto(const Graph* g, sssp_config* c);
 int validate_config(const sssp_config* c);
+// Run-time sampling request (sssp_solve_sampled): host output of cap
+// samples of kTimelineFields words, the period, and the count taken.
+struct Sampling {
+    unsigned long long* out;
+    int32_t cap;
+    int32_t period_us;
+    int32_t* n_out;
+};
+
+// `unit`: breadth-first search (every arc counts 1; u32 levels out).
 int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int32_t src0, int32_t nq,
                 void* dist_out, int32_t* pred_out, const sssp_config* cfg, cudaStream_t stream,
-                sssp_stats* st_out);
+                sssp_stats* st_out, bool unit = false, const Sampling* samp = nullptr);
 
 inline uint32_t __float_as_uint_host(float f) {
     uint32_t b;

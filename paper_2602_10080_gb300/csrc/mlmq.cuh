@@ -101,7 +101,8 @@ struct __align__(128) Ctrl {
     int err_where;
     int err_info;
     unsigned long long slice_end;        // serving: globaltimer value at which the current slice ends (0 = unset)
-    int pad3[26];
+    unsigned long long processed;        // run-time sampling: elements taken for relaxation
+    int pad3[24];
     unsigned long long stats[32];
 };
 
@@ -142,6 +143,7 @@ struct KParams {
     int32_t refillers;       // warps of a block that may refill L1 from L2 at the same time
     int32_t stage;           // 1: heavy-arc writes are pooled per bucket in the block before L2
     int32_t l2_only;         // 1: single-queue baseline (every write to L2, one chunk per read)
+    int32_t unit_w;          // 1: breadth-first search: every real arc weighs 1, a shadow link 0
     int32_t scratch_off, far_off, stat_off, stage_off, l1_off;  // byte offsets in dynamic shared memory
     unsigned long long timeout_ns;
     unsigned long long slice_ns;   // serving: end the launch after this long, draining local queues to L2 (0 = run to completion)
@@ -153,10 +155,11 @@ struct KParams {
     uint32_t timeline_ns;         // sampling period
 };
 
-// Run-time sampling (one lane of block 0): time since start, elements
-// written to L2 (reserve), L2 elements completed (done), the window W, and
-// the warps of block 0 that held a batch at the sampling instant.
-constexpr int kTimelineFields = 5;
+// Run-time sampling (one lane of block 0): time since start (ns), elements
+// written to L2 (reserve), L2 elements completed (done, published per block
+// and so lagging), elements taken for relaxation from any level, the window
+// W, and the warps of block 0 holding a batch at the sampling instant.
+constexpr int kTimelineFields = 6;
 
 // ------------------------------------------------------------------ PTX --
 
@@ -1414,6 +1417,7 @@ struct Worker {
         r.pu = PRED != 0 ? __shfl_sync(kFull, pu, j) : 0u;
         r.in = g < total;
         r.a = r.in ? __ldg(P.adj + (ors + (g - oex))) : make_uint2(0u, 0u);
+        if (P.unit_w) r.a.y = r.a.x >= (uint32_t)P.n ? 0u : 1u;
         return r;
     }
 
@@ -1531,10 +1535,11 @@ struct Worker {
         B->next_sample = now + P.timeline_ns;
         unsigned long long* o = P.timeline + (size_t)B->nsamples * kTimelineFields;
         o[0] = now - B->t0;
+        o[2] = ld_acquire64(&P.ctrl->done);      // done before reserve: done <= reserve
         o[1] = ld_acquire64(&P.ctrl->reserve);
-        o[2] = ld_acquire64(&P.ctrl->done);
-        o[3] = ld_acquire64(&P.ctrl->window);
-        o[4] = *(volatile uint32_t*)&B->busy;
+        o[3] = ld_acquire64(&P.ctrl->processed);
+        o[4] = ld_acquire64(&P.ctrl->window);
+        o[5] = *(volatile uint32_t*)&B->busy;
         B->nsamples++;
     }
 
@@ -1608,7 +1613,12 @@ struct Worker {
             }
             idle_ns = 0;
             mark(7, iter);
-            if (P.timeline && blockIdx.x == 0 && lane == 0) atomicAdd(&S()->busy, 1u);
+            if (P.timeline) {
+                // run-time sampling only: the batch's elements, and block 0's busy warps
+                const uint32_t nb = (uint32_t)__popc(__ballot_sync(kFull, valid));
+                if (lane == 0) atomicAdd(&P.ctrl->processed, (unsigned long long)nb);
+                if (blockIdx.x == 0 && lane == 0) atomicAdd(&S()->busy, 1u);
+            }
             dec += relax_batch(valid, e);
             if (P.timeline && blockIdx.x == 0 && lane == 0) atomicSub(&S()->busy, 1u);
             stat(kCyRelax, (unsigned long long)((unsigned long long)(clock64() - c3)));

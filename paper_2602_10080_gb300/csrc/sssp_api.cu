@@ -123,6 +123,7 @@ __global__ void seed_kernel(KParams P, const int32_t* srcs, int32_t src0, int32_
     __shared__ uint32_t cur_s;
     if (lane == 0) {
         C->reserve = (unsigned long long)nq;
+        C->processed = 0;
         C->done = 0;
         C->finished = 0;
         C->error = 0;
@@ -314,6 +315,7 @@ void Workspace::release() {
     cudaFree(out_d);
     cudaFree(out_p);
     cudaFree(srcs);
+    cudaFree(tl);
     if (host_ctrl) cudaFreeHost(host_ctrl);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -465,9 +467,10 @@ int pred_mode_for(const Graph* g) {
     return (g->wtype == SSSP_W_U32 && g->feat.min_w >= 1.0) ? 1 : 2;
 }
 
-int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, LaunchPlan* out) {
+int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, LaunchPlan* out, bool unit) {
     LaunchPlan& L = *out;
-    L.key = KernelKey{g->wtype == SSSP_W_F32 ? 1 : 0, pred_mode, mq ? 1 : 0};
+    const bool f32 = g->wtype == SSSP_W_F32 && !unit;
+    L.key = KernelKey{f32 ? 1 : 0, pred_mode, mq ? 1 : 0};
     // shared-memory layout of one block
     L.threads = cfg.block_threads;
     const int warps_per_block = L.threads / 32;
@@ -494,7 +497,8 @@ int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, 
     P.nq = 1;
     P.vmask = 0xffffffffu;
     P.shards = cfg.shards;
-    P.delta = g->wtype == SSSP_W_F32 ? __float_as_uint_host(cfg.delta_f32) : cfg.delta_u32;
+    P.delta = f32 ? __float_as_uint_host(cfg.delta_f32) : cfg.delta_u32;
+    P.unit_w = unit ? 1 : 0;
     P.bnum = std::min(cfg.bnum, cfg.bmax);
     P.bmax = cfg.bmax;
     P.l1_type = cfg.l1_type;
@@ -502,7 +506,7 @@ int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, 
     P.wb = cfg.l1_type == SSSP_L1_VECTOR ? cfg.wb : 0;
     P.filter_deltas = cfg.filter_deltas;
     if (cfg.near_deltas > 0.0f) {
-        if (g->wtype == SSSP_W_F32)
+        if (f32)
             P.near_w = __float_as_uint_host(cfg.delta_f32 * cfg.near_deltas);
         else
             P.near_w = (uint32_t)std::min(4294967295.0, (double)cfg.delta_u32 * cfg.near_deltas);
@@ -529,8 +533,9 @@ int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, 
 
 int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int32_t src0, int32_t nq,
                 void* dist_out, int32_t* pred_out, const sssp_config* cfg_in, cudaStream_t stream,
-                sssp_stats* st_out) {
+                sssp_stats* st_out, bool unit, const Sampling* samp) {
     sssp_config cfg = cfg_in ? *cfg_in : (g->tuned_valid ? g->tuned : g->defaults);
+    if (unit && cfg.delta_u32 == 0) cfg.delta_u32 = 1;   // breadth-first: one bucket per level
     resolve_auto(g, &cfg);
     int rc = validate_config(&cfg);
     if (rc) return rc;
@@ -543,9 +548,11 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
         if (vbits == 0) vbits = 1;
         if ((unsigned long long)nq << vbits > (1ull << 32)) return SSSP_E_INVAL;
     }
-    const int pred_mode = pred_out ? pred_mode_for(g) : 0;
+    // unit weights are >= 1: the packed minimum gives the smallest-index parent
+    const int pred_mode = pred_out ? (unit ? 1 : pred_mode_for(g)) : 0;
+    const bool f32 = g->wtype == SSSP_W_F32 && !unit;
     LaunchPlan plan;
-    rc = plan_launch(g, cfg, pred_mode, mq, &plan);
+    rc = plan_launch(g, cfg, pred_mode, mq, &plan, unit);
     if (rc) return rc;
     const KernelKey key = plan.key;
     const int shards = cfg.shards;
@@ -610,18 +617,19 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
             fill_u64_kernel<<<grid_for(cells, g->sms), 256, 0, stream>>>(ws.d64, cells, ~0ull);
         else
             fill_u32_kernel<<<grid_for(cells, g->sms), 256, 0, stream>>>(
-                (uint32_t*)work, cells, g->wtype == SSSP_W_F32 ? kInfF32 : kInfU32);
+                (uint32_t*)work, cells, f32 ? kInfF32 : kInfU32);
         seed_kernel<<<1, 32, 0, stream>>>(P, srcs_d, src0, nq, pred_mode ? 1 : 0);
         cudaEventRecord(ws.ev1, stream);
-        // SSSP_DEBUG >= 4: run-time sampling into mapped host memory, printed after the solve
-        unsigned long long* tl_h = nullptr;
-        const int tl_cap = 4096;
-        if (dbg > 3 && cudaHostAlloc((void**)&tl_h, (size_t)tl_cap * kTimelineFields * 8, cudaHostAllocMapped) ==
-                           cudaSuccess) {
-            std::memset(tl_h, 0xff, (size_t)tl_cap * kTimelineFields * 8);
-            cudaHostGetDevicePointer((void**)&P.timeline, tl_h, 0);
+        // run-time sampling (sssp_solve_sampled, or SSSP_DEBUG >= 4: printed)
+        const bool sampling = samp != nullptr || dbg > 3;
+        const int tl_cap = samp ? samp->cap : 4096;
+        if (sampling) {
+            rc = grow(&ws.tl, &ws.tl_n, (size_t)tl_cap * kTimelineFields);
+            if (rc) return rc;
+            cudaMemsetAsync(ws.tl, 0xff, (size_t)tl_cap * kTimelineFields * 8, stream);
+            P.timeline = ws.tl;
             P.timeline_cap = tl_cap;
-            P.timeline_ns = 20000;
+            P.timeline_ns = (uint32_t)(samp ? samp->period_us : 20) * 1000u;
         }
         unsigned long long* trace_h = nullptr;
         const size_t nthreads_total = (size_t)grid * threads;
@@ -657,8 +665,7 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
                 pp = ws.out_p;
             }
             unpack_kernel<<<grid_for(ocells, g->sms), 256, 0, stream>>>(work, pred_mode ? 1 : 0, nq, n, nv, dd,
-                                                                        pred_mode ? pp : nullptr,
-                                                                        g->wtype == SSSP_W_F32);
+                                                                        pred_mode ? pp : nullptr, f32);
             if (!dist_dev) cudaMemcpyAsync(dist_out, dd, ocells * 4, cudaMemcpyDeviceToHost, stream);
             if (pred_out && !pred_dev) cudaMemcpyAsync(pred_out, pp, ocells * 4, cudaMemcpyDeviceToHost, stream);
         }
@@ -698,14 +705,25 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
             if (dbg) std::fprintf(stderr, "[sssp] stream error: %s\n", cudaGetErrorString(ce));
             return cuda_status(ce);
         }
-        if (tl_h) {
-            std::fprintf(stderr, "[sssp] timeline (us, L2 written, L2 done, window, busy warps of block 0):\n");
-            for (int i = 0; i < tl_cap && tl_h[(size_t)i * kTimelineFields] != ~0ull; i++) {
-                const unsigned long long* o = tl_h + (size_t)i * kTimelineFields;
-                std::fprintf(stderr, "[sssp]   %8.1f %12llu %12llu %8llu %3llu\n", o[0] / 1000.0, o[1], o[2], o[3],
-                             o[4]);
+        if (sampling) {
+            std::vector<unsigned long long> tl((size_t)tl_cap * kTimelineFields);
+            if (cudaMemcpy(tl.data(), ws.tl, tl.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return SSSP_E_CUDA;
+            int ns = 0;
+            while (ns < tl_cap && tl[(size_t)ns * kTimelineFields] != ~0ull) ns++;
+            if (samp) {
+                std::memcpy(samp->out, tl.data(), (size_t)ns * kTimelineFields * 8);
+                *samp->n_out = ns;
             }
-            cudaFreeHost(tl_h);
+            if (dbg > 3) {
+                std::fprintf(stderr, "[sssp] timeline (us, L2 written, L2 done, processed, window, busy warps of "
+                                     "block 0):\n");
+                for (int i = 0; i < ns; i++) {
+                    const unsigned long long* o = tl.data() + (size_t)i * kTimelineFields;
+                    std::fprintf(stderr, "[sssp]   %8.1f %12llu %12llu %12llu %8llu %3llu\n", o[0] / 1000.0, o[1],
+                                 o[2], o[3], o[4], o[5]);
+                }
+            }
         }
         const Ctrl& hc = *ws.host_ctrl;
         float ms_kernel = 0, ms_total = 0;
@@ -1020,6 +1038,38 @@ extern "C" int sssp_solve(sssp_graph* gh, int32_t src, void* dist_out, int32_t* 
     std::lock_guard<std::mutex> lk(g->mu);
     try {
         return run_queries(g, nullptr, nullptr, src, 1, dist_out, pred_out, cfg, (cudaStream_t)stream, nullptr);
+    } catch (...) {
+        return SSSP_E_NOMEM;
+    }
+}
+
+extern "C" int sssp_bfs(sssp_graph* gh, int32_t src, uint32_t* level_out, int32_t* pred_out,
+                        const sssp_config* cfg, void* stream) {
+    if (!gh || !level_out) return SSSP_E_INVAL;
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    if (src < 0 || src >= g->n) return SSSP_E_INVAL;
+    std::lock_guard<std::mutex> lk(g->mu);
+    try {
+        return run_queries(g, nullptr, nullptr, src, 1, level_out, pred_out, cfg, (cudaStream_t)stream, nullptr,
+                           true);
+    } catch (...) {
+        return SSSP_E_NOMEM;
+    }
+}
+
+extern "C" int sssp_solve_sampled(sssp_graph* gh, int32_t src, void* dist_out, int32_t* pred_out,
+                                  const sssp_config* cfg, uint64_t* samples_out, int32_t cap, int32_t period_us,
+                                  int32_t* n_out) {
+    if (!gh || !dist_out || !samples_out || !n_out || cap < 1 || cap > (1 << 24) || period_us < 1)
+        return SSSP_E_INVAL;
+    if (is_device_ptr(samples_out)) return SSSP_E_INVAL;
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    if (src < 0 || src >= g->n) return SSSP_E_INVAL;
+    *n_out = 0;
+    Sampling samp{reinterpret_cast<unsigned long long*>(samples_out), cap, period_us, n_out};
+    std::lock_guard<std::mutex> lk(g->mu);
+    try {
+        return run_queries(g, nullptr, nullptr, src, 1, dist_out, pred_out, cfg, nullptr, nullptr, false, &samp);
     } catch (...) {
         return SSSP_E_NOMEM;
     }

@@ -134,3 +134,10 @@ int main(void) {{
                                            check=True).stdout.split()]
     assert vals == [ctypes.sizeof(sssp.sssp_serve_options), ctypes.sizeof(sssp.sssp_serve_stats),
                     sssp.sssp_serve_options.flags.offset, sssp.sssp_serve_stats.kernel_ms.offset]
+
+
+def test_sampled_rejects_bad_arguments(lib):
+    n = ctypes.c_int32()
+    buf = (ctypes.c_uint64 * 12)()
+    assert lib.sssp_solve_sampled(None, 0, None, None, None, buf, 2, 10, ctypes.byref(n)) == sssp.SSSP_E_INVAL
+    assert lib.sssp_bfs(None, 0, None, None, None, None) == sssp.SSSP_E_INVAL

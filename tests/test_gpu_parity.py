@@ -227,3 +227,65 @@ def test_single_queue_baselines(l2):
         d, p = gpu_solve(G, src, config=c)
         assert_exact(g, src, d, p)
         G.close()
+
+
+def _bfs_reference(g, src):
+    """Levels = unit-weight distances (pinned to BFS levels by the oracle
+    tests), parents = the canonical smallest-index tight in-neighbour."""
+    unit = np.ones(g.m, np.uint32)
+    lev = oracle.dijkstra_u32(g.row_ptr, g.col, unit, int(src))
+    par = oracle.pred_canonical_u32(g.row_ptr, g.col, unit, int(src), lev)
+    return lev, par
+
+
+@pytest.mark.parametrize("name", ["grid256", "rmat14", "randdir_zero", "rmat14f", "hubs"])
+def test_bfs_levels_and_parents(name):
+    if name == "grid256":
+        g, src = gg.workload("grid256"), 0
+    elif name == "rmat14":
+        g, src = gg.rmat(14, 16, lo=1, hi=255, seed=5), None
+    elif name == "randdir_zero":
+        g, src = gg.random_directed(4000, 30000, 0, 20, seed=4), 3
+    elif name == "rmat14f":
+        g, src = gg.rmat(14, 16, seed=6, wtype="f32"), None
+    else:
+        # hub vertices are split into shadows in the device layout
+        g, src = gg.rmat(16, 32, a=0.65, b=0.15, c=0.15, lo=1, hi=9, seed=2), None
+    if src is None:
+        src = int(gg.giant_sources(g, 1)[0][0])
+    G = upload(g)
+    lev_ref, par_ref = _bfs_reference(g, src)
+    for host in (False, True):
+        if host:
+            lev = np.empty(G.n, np.uint32)
+            par = np.empty(G.n, np.int32)
+            G.bfs(src, lev, par)
+        else:
+            lt = torch.empty(G.n, dtype=torch.int32, device="cuda")
+            pt = torch.empty(G.n, dtype=torch.int32, device="cuda")
+            G.bfs(src, lt, pt)
+            torch.cuda.synchronize()
+            lev, par = lt.cpu().numpy().view(np.uint32), pt.cpu().numpy()
+        assert np.array_equal(lev, lev_ref), name
+        assert np.array_equal(par, par_ref), name
+    G.close()
+
+
+def test_solve_sampled_timeline():
+    """Run-time sampling: same results as sssp_solve, and a timeline whose
+    counters move the right way."""
+    g = gg.grid(512, 512, 1, 100, seed=3)
+    G = upload(g)
+    d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    p = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    tl = S.sssp_solve_sampled(G.handle, 0, d, p, cap=8192, period_us=10)
+    torch.cuda.synchronize()
+    assert_exact(g, 0, d.cpu().numpy().view(np.uint32), p.cpu().numpy())
+    assert len(tl) >= 3
+    t, written, done, processed, window = (tl[:, i].astype(np.int64) for i in range(5))
+    assert (np.diff(t) > 0).all()
+    assert (np.diff(written) >= 0).all() and (np.diff(processed) >= 0).all() and (np.diff(done) >= 0).all()
+    assert (done <= written).all()
+    assert processed[-1] > 0 and window.max() > 0
+    assert (tl[:, 5] <= 32).all()
+    G.close()
