@@ -294,6 +294,11 @@ __device__ __forceinline__ void raise_error(Ctrl* C, int code, int where, int in
 
 // The dynamic shared memory of mlmq_kernel (BlockShared, then the regions at
 // the byte offsets in KParams).
+//
+// Code size: the L2 write, the far-staging flush and the block-staging
+// flush are called from many places and are kept out of line
+// (__noinline__), so one copy of each sits in the instruction cache; the
+// relaxation round and the L0/L1 paths stay inline.
 extern __shared__ __align__(16) unsigned char mlmq_smem[];
 
 template <int WT, int PRED, bool MQ, int R>
@@ -479,7 +484,7 @@ struct Worker {
     // chunk of its own.  ctrl.reserve grows BEFORE any chunk is published.
     // Returns the number of elements written (warp-uniform); the caller
     // defers the decrement.
-    __device__ int l2_write(bool valid, uint2 e) {
+    __device__ __noinline__ int l2_write(bool valid, uint2 e) {
         const uint32_t vm = __ballot_sync(kFull, valid);
         if (vm == 0) return 0;
         const long long cw0 = clock64();
@@ -1214,7 +1219,7 @@ struct Worker {
 
     // Moves staged elements to L2: all buckets (all = true, the block ran
     // dry) or only those of the window's first two buckets.
-    __device__ void stage_flush(bool all) {
+    __device__ __noinline__ void stage_flush(bool all) {
         if (!P.stage) return;
         unsigned long long win = 0;
         if (lane == 0) win = window();
@@ -1238,7 +1243,7 @@ struct Worker {
         }
     }
 
-    __device__ void far_flush(uint32_t upto) {
+    __device__ __noinline__ void far_flush(uint32_t upto) {
         if (nfar <= upto) return;
         unsigned long long win = 0;
         if (P.stage && lane == 0) win = window();
