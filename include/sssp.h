@@ -197,7 +197,8 @@ SSSP_API int sssp_graph_features(const sssp_graph *g, sssp_features *out);
  *   src       0 <= src < n.
  *   dist_out  n elements (uint32 or fp32 per the graph), host or device.
  *   pred_out  n int32 or NULL.
- *   cfg       NULL = the graph's tuned configuration (or the default).
+ *   cfg       NULL = the graph's tuned configuration, else its default: the feature
+ *             prior picked at creation from the Table 2 features (Section 3.5).
  *   stream    cudaStream_t or NULL.
  * Returns after completion.  Errors: SSSP_E_INVAL, SSSP_E_TIMEOUT,
  * SSSP_E_NOMEM (queue could not be grown), SSSP_E_CUDA. */
@@ -291,8 +292,8 @@ SSSP_API int sssp_solve_sampled(sssp_graph *g, int32_t src, void *dist_out, int3
  *              (host or device memory).
  *   pred_out   [n] int32 or NULL: the smallest-index parent one level up,
  *              pred[src] = src, -1 when unreachable.
- *   cfg        NULL = the graph's configuration; delta 0 means 1 (one
- *              bucket per level).
+ *   cfg        NULL = the graph's configuration with delta 1 (one bucket
+ *              per level); a given cfg with delta 0 also means 1.
  * Errors as for sssp_solve. */
 SSSP_API int sssp_bfs(sssp_graph *g, int32_t src, uint32_t *level_out, int32_t *pred_out,
                       const sssp_config *cfg, void *stream);

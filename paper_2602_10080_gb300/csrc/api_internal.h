@@ -73,6 +73,7 @@ struct LaunchPlan {
 };
 
 int cuda_status(cudaError_t e);
+sssp_config prior_config(const Graph* g);   // the feature prior (sssp_autotune.cu)
 int pred_mode_for(const Graph* g);
 int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, LaunchPlan* out,
                 bool unit = false);

@@ -535,7 +535,8 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
                 void* dist_out, int32_t* pred_out, const sssp_config* cfg_in, cudaStream_t stream,
                 sssp_stats* st_out, bool unit, const Sampling* samp) {
     sssp_config cfg = cfg_in ? *cfg_in : (g->tuned_valid ? g->tuned : g->defaults);
-    if (unit && cfg.delta_u32 == 0) cfg.delta_u32 = 1;   // breadth-first: one bucket per level
+    // breadth-first: one bucket per level unless the caller chose a delta
+    if (unit && (!cfg_in || cfg.delta_u32 == 0)) cfg.delta_u32 = 1;
     resolve_auto(g, &cfg);
     int rc = validate_config(&cfg);
     if (rc) return rc;
@@ -989,6 +990,8 @@ extern "C" int sssp_graph_create(const int32_t* row_ptr, const int32_t* col_idx,
         f.has_zero_w = hacc.zero_w ? 1 : 0;
         rc = build_layout(g, rp0, adj0, 1024, s);
         f.shadows = g->nv - g->n;
+        // the graph's default configuration: the feature prior (Section 3.5)
+        g->defaults = prior_config(g);
         if (rc == SSSP_OK) {
             rp0 = nullptr;  // owned by the graph now (or freed by the relayout)
             adj0 = nullptr;

@@ -44,6 +44,7 @@ sssp_config prior_config(const Graph* g) {
             c.filter_deltas = 1.0f;
             c.near_deltas = 1.0f;
             c.bnum = 4;
+            c.claim = 8;   // many small buckets of work: fewer, larger L2 reads
             break;
         case kMesh:
             c.l1_type = SSSP_L1_FILTER;
