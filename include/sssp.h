@@ -211,7 +211,10 @@ SSSP_API int sssp_solve(sssp_graph *g, int32_t src, void *dist_out, int32_t *pre
  *   dist_out  nq * n elements, query-major: dist_out[q * n + v].
  *   pred_out  nq * n int32 or NULL.
  * nq * 2^ceil(log2 n) must not exceed 2^32 (the element key packs the query
- * index above the vertex bits).  Errors as sssp_solve. */
+ * index above the vertex bits).  When the library picks delta (cfg NULL,
+ * or a zero delta), the batch uses delta / min(16, max(1, nq / 32)): the
+ * queries supply the parallelism, and narrower buckets cut out-of-order
+ * work.  Errors as sssp_solve. */
 SSSP_API int sssp_solve_batch(sssp_graph *g, const int32_t *srcs, int32_t nq, void *dist_out,
                      int32_t *pred_out, const sssp_config *cfg, void *stream);
 
@@ -311,7 +314,8 @@ SSSP_API int sssp_bfs(sssp_graph *g, int32_t src, uint32_t *level_out, int32_t *
  * queries into free slots before the next slice -- so new queries join
  * while earlier ones are still running.  A query admitted while the
  * lane's bucket window is at W has its buckets shifted by W, so its work
- * is ordered with the work already in flight.  Lanes of different graphs
+ * is ordered with the work already in flight.  A lane uses a quarter of the
+ * graph's delta (it holds many queries under load).  Lanes of different graphs
  * run concurrently on their own streams, sharing the SMs. */
 typedef struct sssp_serve_options {
     size_t  mem_budget_bytes;  /* device bytes for distance slices and L2 rings of all lanes

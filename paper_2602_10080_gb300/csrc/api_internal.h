@@ -79,6 +79,7 @@ int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, 
                 bool unit = false);
 bool is_device_ptr(const void* p);
 void resolve_auto(const Graph* g, sssp_config* c);
+void batch_delta(const Graph* g, sssp_config* c, int div);   // delta / div for multi-query launches
 int validate_config(const sssp_config* c);
 // Run-time sampling request (sssp_solve_sampled): host output of cap
 // samples of kTimelineFields words, the period, and the count taken.
