@@ -2,10 +2,11 @@
 configuration the benchmark times (the graph's prior configuration, 512
 threads x resident blocks per SM, predecessors on).
 
-C1 grid 256^2 from vertex 0; C2 R-MAT-22 single-source; C3 road 4096^2, both
-the prior and the autotuned configuration; C4 256 sources of R-MAT-20 in one
-launch (u32 and f32), checked on sampled queries; C5 the served mix over
-the resident graphs.  Every compared vector is complete: bit-exact u32
+The workloads: grid 256^2 from vertex 0; R-MAT-22 single-source; road
+4096^2 under both the prior and the autotuned configuration; 256 sources of
+R-MAT-20 in one launch (u32 and f32), checked on sampled queries; and the
+served mix over the resident graphs (grid 1024^2, R-MAT 18/20/22,
+ER(2^21, 2^25) f32).  Every compared vector is complete: bit-exact u32
 distances, canonical u32 predecessors (weights >= 1), f32 distances
 bit-exact against the f32 Dijkstra and within 1e-6 relative of f64.
 """
@@ -49,13 +50,13 @@ def _f64_close(g, src, dist_bits):
     assert rel.max(initial=0.0) <= 1e-6, rel.max()
 
 
-def test_c1_grid256_source0():
+def test_grid256_source0():
     g, G = workload("grid256")
     d, p = gpu_solve(G, 0)
     assert_exact(g, 0, d, p)
 
 
-def test_c2_rmat22_single_source():
+def test_rmat22_single_source():
     g, G = workload("rmat22")
     srcs, _ = gg.giant_sources(g, 64, seed=2)
     for s in (int(srcs[0]), int(srcs[37])):
@@ -64,7 +65,7 @@ def test_c2_rmat22_single_source():
 
 
 @pytest.mark.parametrize("tuned", [False, True])
-def test_c3_road4096(tuned):
+def test_road4096(tuned):
     g, G = workload("road4096")
     srcs, _ = gg.giant_sources(g, 16, seed=2)
     cfg = None
@@ -75,7 +76,7 @@ def test_c3_road4096(tuned):
     assert_exact(g, s, d, p)
 
 
-def test_c4_rmat20_batch256_u32():
+def test_rmat20_batch256_u32():
     g, G = workload("rmat20")
     srcs, _ = gg.giant_sources(g, 256, seed=2)
     d, p = gpu_batch(G, srcs, pred=True)
@@ -83,7 +84,7 @@ def test_c4_rmat20_batch256_u32():
         assert_exact(g, int(srcs[q]), d[q], p[q])
 
 
-def test_c4_rmat20_batch256_f32():
+def test_rmat20_batch256_f32():
     g, G = workload("rmat20f")
     srcs, _ = gg.giant_sources(g, 256, seed=2)
     d, _ = gpu_batch(G, srcs, pred=False)
@@ -92,7 +93,7 @@ def test_c4_rmat20_batch256_f32():
         _f64_close(g, int(srcs[q]), d[q])
 
 
-def test_c5_served_mix():
+def test_served_mix_resident_graphs():
     names = ("grid1024", "rmat18", "rmat20", "rmat22", "er21")
     srv = S.sssp_serve_create()
     try:
