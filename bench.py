@@ -43,10 +43,23 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def _strip_comments(src: str) -> str:
+    """C/C++ source without comments and blank lines (the code the hash tracks)."""
+    import re
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    lines = []
+    for line in src.splitlines():
+        line = re.sub(r"//.*", "", line).rstrip()
+        if line:
+            lines.append(line)
+    return "\n".join(lines)
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in ("mlmq.cuh", "kernels_u32.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2602_10080_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_2602_10080_gb300", "csrc", f), encoding="utf-8").read()
+        h.update(_strip_comments(text).encode())
     return h.hexdigest()[:16]
 
 

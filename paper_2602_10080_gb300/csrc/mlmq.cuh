@@ -8,8 +8,10 @@
 //
 //   L0  per warp, in registers: a ring of R rows x 32 lanes (position p lives
 //       in lane p % 32, row (p / 32) % R), FIFO (Section 3.4, "L0 queue").
-//   L1  per thread block, in shared memory, behind a warp-granular lock:
-//       Vector / Near-far / Filter / SLF policies (Section 3.4, Fig. 7).
+//   L1  per thread block, in shared memory: Vector / Near-far / Filter / SLF
+//       policies (Section 3.4, Fig. 7).  Vector and Filter are a lock-free
+//       ring (CAS reservations on head and tail, an empty key per slot);
+//       Near-far and SLF take a warp-granular lock.
 //   L2  whole grid, in global memory: bmax circular delta-buckets
 //       (Section 4.2, "L2 Bucket queue"); every bucket is S rings (shards)
 //       of 32-element chunks moved with one ticket per claim (Section 4.2,
@@ -18,12 +20,12 @@
 // Spill and refill follow the cache-like collaboration of Section 3.2: the
 // worker touches L0; an empty level refills from the next one down, a full
 // level writes back to it.  On this GPU the refill of L1 from L2 is done by
-// ONE warp of the block at a time (the others keep working or wait on
-// shared memory), which keeps the number of agents contending for the L2
-// tickets at the number of blocks instead of the number of warps, and a
-// claim takes several chunks at once.  Vertices improved through a heavy arc
-// (weight above near_deltas * delta) skip the local levels and go to their
-// L2 bucket; only light-arc improvements are processed locally at once --
+// at most `refillers` warps of a block at a time (the others keep working),
+// which bounds the agents contending for the L2 tickets, and a claim takes
+// several chunks at once.  Vertices improved through a heavy arc (weight
+// above near_deltas * delta), or to a distance beyond the window front
+// (W + F) * delta, skip the local levels and go to their L2 bucket; only
+// light-arc improvements inside the front are processed locally at once --
 // the light/heavy arc split of delta-stepping, which keeps local processing
 // from running ahead of the bucket order (the redundant-wavefront concern of
 // Section 2.3).
@@ -263,7 +265,7 @@ template <> struct Arith<1> {
 // ------------------------------------------------------ block shared state --
 
 struct BlockShared {
-    int lock;                     // L1 lock (one warp at a time)
+    int lock;                     // L1 lock of the near-far and SLF policies (one warp at a time)
     int slock;                    // far-write staging lock
     int refill;                   // one warp of the block refills L1 from L2
     uint32_t head, tail;          // L1 ring (V, FQ, SLF) or the near ring (NF)
@@ -1174,7 +1176,7 @@ struct Worker {
     // ---- far staging -------------------------------------------------------
     // Heavy-arc writes wait in a per-warp buffer.  Without block staging they
     // go to L2 in groups of up to 32.  With block staging (P.stage) the warps
-    // of a block pool them per L2 bucket in shared memory under the L1 lock,
+    // of a block pool them per L2 bucket in shared memory under the staging lock,
     // and only full 32-element chunks go to L2 -- one warp's writes spread
     // over many buckets, so this is what keeps the chunks full.  Writes for
     // the window's first two buckets are urgent and go to L2 at once; partial

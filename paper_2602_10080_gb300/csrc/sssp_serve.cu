@@ -8,7 +8,8 @@
 // of the persistent MLMQ kernel that stops after slice_us and drains its
 // L0/L1/staging queues into L2 (so the whole queue state lives in L2
 // between launches).  Between slices the host
-//   1. counts every slot's elements left in the L2 rings (scan kernel);
+//   1. reads every slot's count of elements left in the L2 rings (the kernel
+//      keeps the counts: an L2 write adds, an L2 read subtracts);
 //      a slot with none is finished: its distances are final (Eq. 1 holds
 //      for every arc once no improved vertex is left to relax);
 //   2. copies finished results to the callers' buffers and frees the slots;
