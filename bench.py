@@ -63,9 +63,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+TRAFFIC_CONFIG_KEYS = ("l1_type", "l2_type", "delta_u32", "bnum", "bmax", "claim", "block_threads")
+
+
+def config_signature(cfg) -> str:
+    d = cfg.as_dict()
+    return ",".join(f"{k}={d[k]}" for k in TRAFFIC_CONFIG_KEYS)
+
+
+def profiled_traffic(signature=None):
     """Per-launch DRAM bytes of the relaxation kernel from the committed ncu
-    summary, or None if the kernel source changed since it was captured."""
+    summary, or None if the kernel source or the configuration changed
+    since it was captured."""
     p = os.path.join(ROOT, "profiles", "mlmq_kernel_rmat22_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -75,6 +84,8 @@ def profiled_traffic():
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
     if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    if signature is not None and vals.get("config") != signature:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -527,7 +538,7 @@ def main():
     kms = float(np.mean(kernel_ms))
     achieved = alg_bytes / (kms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": profiled_traffic(),
+            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": profiled_traffic(config_signature(tuned)),
             "peak_source": peaks["source"], "kernel": "mlmq_kernel", "kernel_ms_mean": round(kms, 4),
             "alg_bytes_per_launch": int(alg_bytes)}
 

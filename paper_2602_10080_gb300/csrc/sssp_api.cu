@@ -441,7 +441,12 @@ void resolve_auto(const Graph* g, sssp_config* c) {
 // wide buckets: narrower buckets (delta / div) cut the out-of-order work
 // that the shared window admits.  On GB300, 256 R-MAT-20 sources run 1.6x
 // (u32) to 2.4x (f32) faster with delta / 8 than with the single-source delta.
+// The width starts from the general weight-based delta (not a per-family
+// single-source tuning of it).
 void batch_delta(const Graph* g, sssp_config* c, int div) {
+    c->delta_u32 = 0;
+    c->delta_f32 = 0.0f;
+    resolve_auto(g, c);
     if (div <= 1) return;
     if (g->wtype == SSSP_W_F32) c->delta_f32 = c->delta_f32 / (float)div;
     else c->delta_u32 = std::max<uint32_t>(1u, c->delta_u32 / (uint32_t)div);
@@ -549,7 +554,10 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
     if (unit && (!cfg_in || cfg.delta_u32 == 0)) cfg.delta_u32 = 1;
     const bool lib_delta = !cfg_in || (g->wtype == SSSP_W_F32 ? !(cfg_in->delta_f32 > 0.0f) : cfg_in->delta_u32 == 0);
     resolve_auto(g, &cfg);
-    if (nq > 1 && !unit && lib_delta) batch_delta(g, &cfg, std::min(16, std::max(1, nq / 32)));
+    if (nq > 1 && !unit && lib_delta) {
+        batch_delta(g, &cfg, std::min(16, std::max(1, nq / 32)));
+        cfg.bnum = std::min(cfg.bnum, 4);   // the batch width was measured with 4 active buckets
+    }
     int rc = validate_config(&cfg);
     if (rc) return rc;
     if (cudaSetDevice(g->device) != cudaSuccess) return SSSP_E_CUDA;

@@ -512,6 +512,7 @@ Lane* lane_create(sssp_server* s, Graph* g, int pred_mode, int* rc) {
     }
     resolve_auto(g, &cfg);
     batch_delta(g, &cfg, 4);   // a lane holds many queries at load: narrower buckets
+    cfg.bnum = std::min(cfg.bnum, 4);
     *rc = validate_config(&cfg);
     if (!*rc) *rc = plan_launch(g, cfg, pred_mode, true, &L->plan);
     if (*rc) {
