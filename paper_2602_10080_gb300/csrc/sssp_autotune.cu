@@ -43,7 +43,7 @@ sssp_config prior_config(const Graph* g) {
             c.l2_type = SSSP_L2_BUCKET;
             c.filter_deltas = 1.0f;
             c.near_deltas = 1.0f;
-            c.bnum = 8;
+            c.bnum = 16;
             c.claim = 8;   // many small buckets of work: fewer, larger L2 reads
             break;
         case kMesh:
@@ -67,11 +67,11 @@ sssp_config prior_config(const Graph* g) {
     c.delta_f32 = 0.0f;
     resolve_auto(g, &c);
     if (family_of(f) == kPowerLaw) {
-        // half the general width: the hubs supply the parallelism (a GB300
-        // sweep on R-MAT-22 found delta = 2 * avg_w / avg_deg and 8 active
-        // buckets fastest)
-        if (g->wtype == SSSP_W_F32) c.delta_f32 *= 0.5f;
-        else c.delta_u32 = std::max<uint32_t>(1u, c.delta_u32 / 2u);
+        // a quarter of the general width with 16 active buckets (the same
+        // active distance range, finer buckets): the hubs supply the
+        // parallelism; fastest in a GB300 sweep on R-MAT-22
+        if (g->wtype == SSSP_W_F32) c.delta_f32 *= 0.25f;
+        else c.delta_u32 = std::max<uint32_t>(1u, c.delta_u32 / 4u);
     }
     return c;
 }
