@@ -848,6 +848,25 @@ int collect_lane(sssp_server* s, Lane* L) {
             const bool occupied = L->slot_q[k] || L->drain[k];
             if (!occupied) continue;
             Query* q = L->slot_q[k];
+            if ((int32_t)L->live_h[k] < 0) {
+                // an impossible count (more L2 reads than writes): the lane's
+                // accounting is broken; its queries fail and it starts over
+                if (s->debug) std::fprintf(stderr, "[sssp serve] negative L2 count %d in slot %u\n",
+                                           (int32_t)L->live_h[k], k);
+                {
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    for (uint32_t j = 0; j < L->cap; j++) {
+                        if (L->slot_q[j] && !L->slot_q[j]->cancel) finish_query(s, L->slot_q[j], SSSP_E_CUDA);
+                        L->slot_q[j] = nullptr;
+                        L->drain[j] = 0;
+                    }
+                    s->cv_done.notify_all();
+                }
+                L->free_slots.clear();
+                for (uint32_t j = L->cap; j-- > 0;) L->free_slots.push_back(j);
+                L->running = L->draining = 0;
+                return lane_rings_fresh(s, L, L->rings.nch) == SSSP_E_CUDA ? SSSP_E_CUDA : SSSP_OK;
+            }
             bool timed_out = false;
             if (q && s->opt.query_timeout_ms > 0 &&
                 std::chrono::duration<double, std::milli>(now - q->t_admit).count() > s->opt.query_timeout_ms)
