@@ -32,6 +32,7 @@ extern "C" const char* sssp_strerror(int status) {
         case SSSP_E_BUSY: return "server busy";
         case SSSP_E_NODEV: return "no CUDA device";
         case SSSP_E_NOTFOUND: return "unknown ticket";
+        case SSSP_E_CANCELLED: return "query cancelled";
         default: return "unknown status";
     }
 }
