@@ -107,10 +107,11 @@ typedef struct sssp_config {
     float delta_f32;       /* bucket width for f32 graphs (0 = derived from the weights) */
     int32_t bnum;          /* buckets a read may take from, counted from the lowest non-empty (1..32) */
     int32_t bmax;          /* buckets in total, a circular window (1..32; 1 = L2V) */
-    float filter_deltas;   /* L1FQ: F = window base + filter_deltas * delta */
+    float filter_deltas;   /* the window front: F = (window base + filter_deltas) * delta.  L1FQ
+                              keeps elements <= F, and a light-arc write stays local only up to F */
     float near_deltas;     /* light-arc bound in deltas: a write through an arc of weight
-                              <= near_deltas * delta enters L0/L1, a heavier one goes to its L2
-                              bucket (0 = every write enters L0, as in Listing 1) */
+                              <= near_deltas * delta, to a distance <= F, enters L0/L1; any other
+                              goes to its L2 bucket (0 = every write enters L0, as in Listing 1) */
     int32_t max_arcs;      /* arcs one warp relaxes per batch; later vertices wait in L0 (>= 32) */
     int32_t claim;         /* L2 chunks one L1 refill claims at once (1..8) */
     int32_t shards;        /* rings per L2 bucket (1, 2, 4, 8, 16 or 32) */
@@ -142,9 +143,11 @@ typedef struct sssp_features {
 typedef struct sssp_stats {
     double kernel_ms;             /* persistent relaxation kernel, CUDA-event time */
     double total_ms;              /* whole call on the device: init + kernel + outputs */
-    int64_t reached;              /* vertices with finite distance (sum over queries) */
-    int64_t reached_arcs;         /* arcs out of reached vertices, m_r (sum over queries) */
-    int64_t pops_l0, pops_l1, pops_l2, pops_heavy;
+    int64_t reached;              /* -1: not counted by the library (count finite distances
+                                     in the output) */
+    int64_t reached_arcs;         /* -1: not counted (m_r: arcs out of reached vertices) */
+    int64_t pops_l0, pops_l1, pops_l2; /* batches read from each level */
+    int64_t pops_heavy;           /* 0 (reserved) */
     int64_t relax_arcs;           /* arcs scanned (work) */
     int64_t improved;             /* successful relaxations (writes back) */
     int64_t stale;                /* popped elements already superseded */
@@ -179,6 +182,9 @@ SSSP_API int sssp_config_default(sssp_config *cfg);
  *   n >= 1, 0 <= m < 2^31.
  *   *out     receives a new handle owning device memory; free it with
  *            sssp_graph_destroy.
+ * The graph's default configuration is the feature prior: the Table 2
+ * features pick a family (power-law, mesh or road) and its settings
+ * (Section 3.5).
  * Errors: SSSP_E_INVAL (NULL/negative sizes), SSSP_E_BADGRAPH (validation),
  * SSSP_E_NOMEM, SSSP_E_CUDA, SSSP_E_NODEV.  Cites: Section 2.1 (G(V,E,W)),
  * Listing 2 (edge_list / edge_weight). */
@@ -269,6 +275,8 @@ SSSP_API int sssp_autotune(sssp_graph *g, const int32_t *srcs, int32_t nsrc, int
 SSSP_API int sssp_solve_noalloc(const int32_t *row_ptr, const uint32_t *arcs, int32_t n, int64_t m,
                                 int32_t wtype, int32_t src, void *dist_out, int32_t *pred_out,
                                 void *stream);
+
+/* -------------------------------------------------------- run-time sampling -- */
 
 /* Run-time behaviour of one solve (Section 5.3 follows active warps and
  * processed vertices over time): sssp_solve plus a timeline sampled every
