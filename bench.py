@@ -148,6 +148,37 @@ def dist_env():
     return ws, rank, local
 
 
+def percentiles(values) -> dict:
+    """p50, p99 and mean of a list of numbers (3 decimals)."""
+    a = np.asarray(values, dtype=np.float64)
+    if a.size == 0:
+        return {"p50": None, "p99": None, "mean": None}
+    return {"p50": round(float(np.percentile(a, 50)), 3), "p99": round(float(np.percentile(a, 99)), 3),
+            "mean": round(float(a.mean()), 3)}
+
+
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or implementer/part on Arm)."""
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        import platform
+        return platform.machine()
+    for line in info.splitlines():
+        if line.lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    impl = part = None
+    for line in info.splitlines():
+        if line.startswith("CPU implementer") and impl is None:
+            impl = line.split(":", 1)[1].strip()
+        if line.startswith("CPU part") and part is None:
+            part = line.split(":", 1)[1].strip()
+    if impl or part:
+        return f"implementer {impl}, part {part}"
+    import platform
+    return platform.machine()
+
+
 def rank_sources(srcs, rank: int, ws: int) -> list:
     """This rank's share of the sources: every ws-th one from `rank` (weak
     scaling; the ranks' shares are disjoint and cover all sources)."""
@@ -497,7 +528,7 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kernel_ms, arcs, verts, relaxed = [], 0, 0, 0
+    kernel_ms, step_arcs, arcs, verts, relaxed = [], [], 0, 0, 0
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -506,6 +537,7 @@ def main():
             G.solve(s, dist_t, pred_t, None, stream)
             st = S.sssp_last_stats(G.handle)
             kernel_ms.append(st.kernel_ms)
+            step_arcs.append(mr[s])
             relaxed += st.relax_arcs
             arcs += mr[s]
             verts += nr[s]
@@ -559,6 +591,8 @@ def main():
         "gpu_launches": 4 * args.steps,
         "roofline": roof,
         "clocks": clk.summary(),
+        "per_source": {"kernel_ms": percentiles(kernel_ms),
+                       "gteps": percentiles([a / (k / 1e3) / 1e9 for a, k in zip(step_arcs, kernel_ms) if k > 0])},
         "work": {"relaxed_arcs_per_reached_arc": round(relaxed / max(1, arcs / ws), 3),
                  "last": {k: stats[k] for k in ("pops_l0", "pops_l1", "pops_l2", "refills", "improved",
                                                 "stale", "l2_chunks_written", "far_pushes", "grid_blocks",
@@ -571,7 +605,8 @@ def main():
         cg, cdt, _ = cpu_oracle_gteps(g, sample, cores)
         line["cpu_baseline"] = {"value": round(cg, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
                                 "sample": f"{cores} single-source Dijkstra runs on {args.workload}, "
-                                          f"one per thread ({cdt:.1f} s)"}
+                                          f"one per thread ({cdt:.1f} s)",
+                                "single_thread_s_per_query": round(cdt, 3), "cpu_model": cpu_model()}
     if rank == 0 and not args.no_extras:
         line["batch"] = [batch_leg(S, gg, torch, "u32"), batch_leg(S, gg, torch, "f32")]
         line["bfs"] = bfs_leg(S, G, g, srcs_all, torch)

@@ -39,3 +39,11 @@ def test_rank_sources_cover_and_are_disjoint():
     srcs = list(range(10))
     shares = [bench.rank_sources(srcs, r, 3) for r in range(3)]
     assert sorted(sum(shares, [])) == srcs
+
+
+def test_percentiles_and_cpu_model():
+    p = bench.percentiles([1.0, 2.0, 3.0, 4.0, 100.0])
+    assert p["p50"] == 3.0 and p["mean"] == 22.0 and 4.0 < p["p99"] <= 100.0
+    assert bench.percentiles([]) == {"p50": None, "p99": None, "mean": None}
+    m = bench.cpu_model()
+    assert isinstance(m, str) and m
