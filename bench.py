@@ -33,6 +33,9 @@ BYTES_PER_ARC = 12      # col 4 B + weight 4 B + dist[v] check 4 B
 BYTES_PER_VERTEX = 32   # row_ptr 8 B + dist 4 B + pred 4 B + queue push/pop of an 8 B element
 WORKLOAD = "rmat22"
 N_SOURCES = 64
+WORK_KEYS = ("relax_arcs", "relax_shadow", "improved", "stale", "dup_targets", "rounds", "pops_l0", "pops_l1",
+             "pops_l2", "refills", "refill_tries", "cas_fail", "l2_chunks_written", "far_pushes", "idle_iters",
+             "wait_spins", "lock_spins")
 
 
 def measured_peaks() -> dict:
@@ -402,8 +405,6 @@ def serve_leg(S, gg, torch, rates, seconds: float, max_queries: int, graph_cache
             srcs, _ = gg.giant_sources(g, 4096, seed=2)
             graph_cache[name] = (g, G, srcs)
         graphs.append(graph_cache[name])
-    nbuf = 64
-    bufs = [[torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(nbuf)] for g, _, _ in graphs]
     out = []
     for ri, rate in enumerate(rates):
         count = int(max(20, min(max_queries, rate * seconds)))
@@ -415,39 +416,36 @@ def serve_leg(S, gg, torch, rates, seconds: float, max_queries: int, graph_cache
             gi = min(int(ug[i] * len(graphs)), len(graphs) - 1)
             srcs = graphs[gi][2]
             trace.append((float(arr[i]), gi, int(srcs[min(int(us[i] * len(srcs)), len(srcs) - 1)])))
+        # one output buffer per query: submission is never held back
+        bufs = [torch.empty(graphs[gi][0].n, dtype=torch.int32, device="cuda") for _, gi, _ in trace]
         # --- served
         srv = S.sssp_serve_create(slice_us=1000)
         try:
             # warm the lanes (allocation, first launch) outside the trace
-            warm = [S.sssp_serve_submit(srv, G.handle, int(srcs[0]), bufs[gi][0], None)
-                    for gi, (_, G, srcs) in enumerate(graphs)]
+            wbufs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g, _, _ in graphs]
+            warm = [S.sssp_serve_submit(srv, G.handle, int(srcs[0]), wb, None)
+                    for (g, G, srcs), wb in zip(graphs, wbufs)]
             for t in warm:
                 S.sssp_serve_wait(srv, t, -1)
-            last_ticket = [[None] * nbuf for _ in graphs]
-            used = [0] * len(graphs)
-            tickets = []
+            tickets, late = [], []
             t0 = time.perf_counter()
-            for at, gi, src in trace:
+            for i, (at, gi, src) in enumerate(trace):
                 now = time.perf_counter() - t0
                 if at > now:
                     time.sleep(at - now)
-                slot = used[gi] % nbuf
-                used[gi] += 1
-                if last_ticket[gi][slot] is not None:      # buffer still in use
-                    S.sssp_serve_wait(srv, last_ticket[gi][slot], -1)
-                t = S.sssp_serve_submit(srv, graphs[gi][1].handle, src, bufs[gi][slot], None)
-                last_ticket[gi][slot] = t
-                tickets.append(t)
+                late.append(time.perf_counter() - t0 - at)     # submit time - scheduled arrival
+                tickets.append(S.sssp_serve_submit(srv, graphs[gi][1].handle, src, bufs[i], None))
             for t in tickets:
                 st, code = S.sssp_serve_wait(srv, t, -1)
                 if st != S.Q_DONE:
                     raise RuntimeError(f"served query failed: {S.strerror(code)}")
             t_end = time.perf_counter() - t0
-            lat = np.array([S.sssp_serve_latency_us(srv, t) for t in tickets]) / 1e3
+            # latency from the scheduled arrival: (submit - arrival) + (submit -> DONE)
+            lat = np.array([S.sssp_serve_latency_us(srv, t) / 1e3 + 1e3 * lt for t, lt in zip(tickets, late)])
             sstats = S.sssp_serve_get_stats(srv)
         finally:
             S.sssp_serve_destroy(srv)
-        # --- one at a time (FIFO over the same trace)
+        # --- one at a time (FIFO over the same trace), latency from the scheduled arrival
         stream = torch.cuda.current_stream()
         plat = []
         t0 = time.perf_counter()
@@ -455,12 +453,13 @@ def serve_leg(S, gg, torch, rates, seconds: float, max_queries: int, graph_cache
             now = time.perf_counter() - t0
             if at > now:
                 time.sleep(at - now)
-            graphs[gi][1].solve(src, bufs[gi][i % nbuf], None, None, stream)
+            graphs[gi][1].solve(src, bufs[i], None, None, stream)
             torch.cuda.synchronize()
             plat.append((time.perf_counter() - t0 - at) * 1e3)
         p_end = time.perf_counter() - t0
         plat = np.array(plat)
-        out.append({"rate_qps": rate, "queries": count,
+        del bufs
+        out.append({"rate_qps": rate, "queries": count, "arrival_span_s": round(float(trace[-1][0]), 2),
                     "served": {"qps": round(count / t_end, 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
                                "p99_ms": round(float(np.percentile(lat, 99)), 3),
                                "joined_running": sstats["joined_running"],
@@ -469,7 +468,10 @@ def serve_leg(S, gg, torch, rates, seconds: float, max_queries: int, graph_cache
                                     "p50_ms": round(float(np.percentile(plat, 50)), 3),
                                     "p99_ms": round(float(np.percentile(plat, 99)), 3)}})
     return {"graphs": list(SERVE_GRAPHS), "arrivals": "Poisson, seed 3; graph uniform, source uniform over "
-                                                       "the giant component", "results": out}
+                                                       "the giant component",
+            "latency": "p50/p99 from each query's scheduled arrival to its result, both arms; served = "
+                       "(submit - arrival) + the server's submit-to-DONE time",
+            "results": out}
 
 
 def main():
@@ -482,8 +484,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tune-ms", type=int, default=0,
                     help="timed autotune budget in ms (0 = the feature-based prior configuration)")
-    ap.add_argument("--serve-rates", default="100,1000", help="serving leg arrival rates (q/s)")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival span per rate")
+    ap.add_argument("--serve-rates", default="10,30,100,300,1000,2000", help="serving leg arrival rates (q/s)")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="arrival span per rate at most")
     ap.add_argument("--serve-max", type=int, default=2000, help="queries per rate at most")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -529,6 +531,8 @@ def main():
         torch.distributed.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kernel_ms, step_arcs, arcs, verts, relaxed = [], [], 0, 0, 0
+    work_sum = {k: 0 for k in WORK_KEYS}
+    cyc_sum = np.zeros(6)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -539,6 +543,9 @@ def main():
             kernel_ms.append(st.kernel_ms)
             step_arcs.append(mr[s])
             relaxed += st.relax_arcs
+            for k in WORK_KEYS:
+                work_sum[k] += getattr(st, k)
+            cyc_sum += np.array(list(st.cycles), dtype=np.float64)
             arcs += mr[s]
             verts += nr[s]
         ev1.record(stream)
@@ -564,6 +571,16 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_value = e2e_arcs / e2e_s / 1e9 * ws
 
+    # L2 residency from the device's own L2 size: the CSR streamed from HBM,
+    # the distance words (8 B per layout vertex with predecessors) re-used
+    l2_bytes = int(torch.cuda.get_device_properties(local).L2_cache_size)
+    csr_bytes = 8 * g.m + 4 * (g.n + 1)
+    dist_bytes = 8 * G.features()["shadows"] + 8 * g.n
+    l2_note = (f"inputs larger than L2 (CSR {csr_bytes / 1e9:.2f} GB > L2 {l2_bytes / 2**20:.0f} MiB), no flush"
+               if csr_bytes > l2_bytes else f"CSR {csr_bytes / 1e6:.0f} MB fits in L2 ({l2_bytes / 2**20:.0f} MiB)")
+    l2_res = {"l2_bytes": l2_bytes, "csr_bytes": csr_bytes, "dist_bytes": dist_bytes,
+              "csr_fits": csr_bytes <= l2_bytes, "dist_fits": dist_bytes <= l2_bytes}
+
     peaks = measured_peaks()
     # roofline of the relaxation kernel: algorithmic bytes per launch / kernel time
     alg_bytes = (BYTES_PER_ARC * arcs + BYTES_PER_VERTEX * verts) / (args.steps * ws)
@@ -581,7 +598,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"{args.workload} single-source (R-MAT scale 22, ef 16, a/b/c/d .57/.19/.19/.05, "
                                "u32 [1,255], symmetrised, dedup); 64 giant-component sources, each solved alone",
-                   "n": g.n, "m": g.m, "giant": giant, "l2_flush": "inputs larger than L2 (CSR 1.07 GB)",
+                   "n": g.n, "m": g.m, "giant": giant, "l2_flush": l2_note,
+                   "l2_residency": l2_res,
                    "queue": {k: v for k, v in tuned.as_dict().items()
                              if k in ("l1_type", "l2_type", "delta_u32", "bnum", "bmax", "wb",
                                       "filter_deltas", "th_heavy", "block_threads")},
@@ -594,19 +612,30 @@ def main():
         "per_source": {"kernel_ms": percentiles(kernel_ms),
                        "gteps": percentiles([a / (k / 1e3) / 1e9 for a, k in zip(step_arcs, kernel_ms) if k > 0])},
         "work": {"relaxed_arcs_per_reached_arc": round(relaxed / max(1, arcs / ws), 3),
-                 "last": {k: stats[k] for k in ("pops_l0", "pops_l1", "pops_l2", "refills", "improved",
-                                                "stale", "l2_chunks_written", "far_pushes", "grid_blocks",
-                                                "block_threads")}},
+                 "per_solve_mean": {k: int(v / args.steps) for k, v in work_sum.items()},
+                 "warp_cycle_split": {k: round(float(c / max(1.0, cyc_sum.sum())), 3)
+                                      for k, c in zip(S.sssp_stats.CYCLE_NAMES, cyc_sum)},
+                 "cas_fail_per_refill": round(work_sum["cas_fail"] / max(1, work_sum["refills"]), 2),
+                 "grid_blocks": stats["grid_blocks"], "block_threads": stats["block_threads"]},
     }
     if rank == 0 and not args.no_extras:
         # the oracle timed on this host's cores on a bounded sample of the same workload
         cores = max(1, min(16, os.cpu_count() or 1))
         sample = [int(s) for s in srcs_all[:cores]]
         cg, cdt, _ = cpu_oracle_gteps(g, sample, cores)
+        # one query alone on one core (nothing else running), for a few sources
+        single = []
+        for s in srcs_all[:3]:
+            _, dt1, _ = cpu_oracle_gteps(g, [int(s)], 1)
+            single.append(dt1)
         line["cpu_baseline"] = {"value": round(cg, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
                                 "sample": f"{cores} single-source Dijkstra runs on {args.workload}, "
-                                          f"one per thread ({cdt:.1f} s)",
-                                "single_thread_s_per_query": round(cdt, 3), "cpu_model": cpu_model()}
+                                          f"one per thread, all at once ({cdt:.1f} s)",
+                                "single_thread_s_per_query": {"p50": round(float(np.median(single)), 3),
+                                                              "max": round(float(np.max(single)), 3),
+                                                              "sample": f"{len(single)} sources, one at a time "
+                                                                        "on one core"},
+                                "all_core_s_per_query": round(cdt / cores, 3), "cpu_model": cpu_model()}
     if rank == 0 and not args.no_extras:
         line["batch"] = [batch_leg(S, gg, torch, "u32"), batch_leg(S, gg, torch, "f32")]
         line["bfs"] = bfs_leg(S, G, g, srcs_all, torch)

@@ -125,7 +125,19 @@ typedef struct sssp_config {
                               L0/L1, no block staging, one chunk per read); with l2_type
                               SSSP_L2_BUCKET this is a delta-stepping (L2DQ-only) queue, with
                               SSSP_L2_VECTOR a single FIFO (Section 2.2's single-queue designs) */
-    int32_t reserved[2];   /* must be zero */
+    int32_t split_arcs;    /* hub split threshold: a vertex with more arcs is represented by
+                              zero-weight shadow vertices owning at most split_arcs arcs each
+                              (0 = the default 1024; else 32..2^30).  The layout is a property
+                              of the graph: a solve whose value differs from the graph's
+                              current layout rebuilds it first (one pass over the CSR), and
+                              returns SSSP_E_BUSY while a server has a lane on the graph */
+    int32_t hub_bnum;      /* > 0: shadow vertices (slices of split hubs) get their own rings (the
+                              upper half of each bucket's shards; needs shards >= 2) and are read
+                              only from the first hub_bnum non-empty buckets, so a hub is expanded
+                              once its distance is near the front (0 = they share the rings) */
+    int32_t dedup;         /* 1: a warp round writes each improved target once, with the smallest
+                              distance (in-warp duplicates, matched with __match_any_sync) */
+    int32_t reserved;      /* must be zero */
 } sssp_config;
 
 /* Graph features of Table 2 (Section 3.5), computed at creation. */
@@ -159,6 +171,19 @@ typedef struct sssp_stats {
                                      L2/task read, idle, L0 read */
     int32_t grid_blocks, block_threads;
     int32_t attempts;             /* > 1 if the queue was regrown after an overflow */
+    int32_t pad0;
+    int64_t dup_targets;          /* improved arcs whose target another improved arc of the same
+                                     warp round shares (in-warp duplicates, Listing 1's write) */
+    int64_t rounds;               /* 32-arc relaxation rounds of all warps */
+    int64_t refill_tries;         /* L1 refill attempts from L2 (refills = the successful ones) */
+    int64_t wait_spins;           /* spins on L2 chunk sequence words (writer and reader waits) */
+    int64_t idle_iters;           /* worker iterations that found no work anywhere */
+    int64_t window_pull_backs;    /* L2 writes below the bucket window (window moved back) */
+    int64_t window_advances;      /* window moves forward past empty buckets */
+    int64_t lock_spins;           /* spins on the block locks (L1 near-far / SLF, block staging) */
+    int64_t cycles_fine[3];       /* SM cycles in relaxation rounds (loads + atomics), in their
+                                     pushes, and in batch set-up; zero unless the library is built
+                                     with SSSP_FINE_CYCLES=1 */
 } sssp_stats;
 
 typedef struct sssp_graph sssp_graph;
@@ -174,9 +199,10 @@ SSSP_API int sssp_config_default(sssp_config *cfg);
 
 /* Copies a CSR graph to the device, validates it and derives the layout the
  * kernels use: interleaved (col, weight) pairs (one 8-byte load per arc),
- * and every vertex with more than `split` arcs (1024) represented by
- * zero-weight shadow vertices that each own a slice of at most `split`
- * arcs, so the arcs of a hub are relaxed by many warps at once.
+ * and every vertex with more than 1024 arcs (the default of
+ * sssp_config.split_arcs) represented by zero-weight shadow vertices that
+ * each own a slice of at most that many arcs, so the arcs of a hub are
+ * relaxed by many warps at once.
  *   row_ptr  int32[n + 1], col_idx int32[m], weights uint32[m] or fp32[m]
  *            (per `wtype`); host or device memory, borrowed (copied).
  *   n >= 1, 0 <= m < 2^31.
@@ -217,10 +243,12 @@ SSSP_API int sssp_solve(sssp_graph *g, int32_t src, void *dist_out, int32_t *pre
  *   dist_out  nq * n elements, query-major: dist_out[q * n + v].
  *   pred_out  nq * n int32 or NULL.
  * nq * 2^ceil(log2 n) must not exceed 2^32 (the element key packs the query
- * index above the vertex bits).  When the library picks delta (cfg NULL,
- * or a zero delta), the batch uses delta / min(16, max(1, nq / 32)): the
- * queries supply the parallelism, and narrower buckets cut out-of-order
- * work.  Errors as sssp_solve. */
+ * index above the vertex bits).  With cfg NULL the batch uses the
+ * configuration sssp_autotune_batch cached for its size class, if any.
+ * Otherwise, when the library picks delta (cfg NULL, or a zero delta), the
+ * batch uses delta / min(16, max(1, nq / 32)) with bnum <= 4: the queries
+ * supply the parallelism, and narrower buckets cut out-of-order work.
+ * Errors as sssp_solve. */
 SSSP_API int sssp_solve_batch(sssp_graph *g, const int32_t *srcs, int32_t nq, void *dist_out,
                      int32_t *pred_out, const sssp_config *cfg, void *stream);
 
@@ -237,6 +265,24 @@ SSSP_API int sssp_last_stats(const sssp_graph *g, sssp_stats *out);
  * *out when out != NULL.  budget_ms <= 0 returns the prior untimed. */
 SSSP_API int sssp_autotune(sssp_graph *g, const int32_t *srcs, int32_t nsrc, int32_t budget_ms,
                   sssp_config *out);
+
+/* Picks a configuration for multi-query launches (sssp_solve_batch) of about
+ * nq queries: Section 3.5's input-adaptive configuration applied to the
+ * batched launch.  It starts from the graph's configuration with the
+ * library's multi-query bucket width (delta / min(16, nq / 32), bnum <= 4)
+ * and, within about budget_ms, times one whole batch launch from the given
+ * sources per candidate: the bucket-width divisor, bnum, the L1 depth, the
+ * claim size, the refill concurrency and the hub rings.  The winner is cached
+ * on the graph for launches of the same size class (nq rounded down to a
+ * power of two) made with cfg == NULL; serving lanes of the graph created
+ * afterwards use the winner of the largest class.  budget_ms == 0 caches the
+ * starting point untimed.
+ *   srcs   int32[nq], host or device, each in [0, n); nq >= 2.
+ *   out    receives the configuration (may be NULL).
+ * Errors: SSSP_E_INVAL, SSSP_E_NOMEM (the nq * n distance buffer of the
+ * timed launches), SSSP_E_CUDA. */
+SSSP_API int sssp_autotune_batch(sssp_graph *g, const int32_t *srcs, int32_t nq, int32_t budget_ms,
+                                 sssp_config *out);
 
 /* ---------------------------------------------------------- no allocation -- */
 
@@ -255,12 +301,15 @@ SSSP_API int sssp_autotune(sssp_graph *g, const int32_t *srcs, int32_t nsrc, int
  * every piece of scratch state (control block, L2 rings, packed
  * distance/predecessor words) in one array of about 25 MiB that is part of
  * the library image: every GPU that loads the library holds it until the
- * process exits.  The first call on a device sets that array up (resolving
- * its device address and emptying the queue metadata), so make the first
- * call before any stream capture.  All calls share the array and it keeps
- * the last call's contents; each call re-initialises what must start empty.
- * Calls serialise on a process-wide lock and return only after the GPU work
- * has finished; two calls that overlapped on the GPU would race on the array.
+ * process exits.  The first call on a device resolves that array's device
+ * address.  All calls share the array and it keeps the last call's contents;
+ * every call first re-initialises what must start empty (queue metadata,
+ * control block, distance words), so a call does not depend on how the
+ * previous one ended.  Calls serialise on a process-wide lock and return only
+ * after the GPU work has finished; two calls that overlapped on the GPU would
+ * race on the array.  Every call reads a status back and synchronises its
+ * stream part-way, so no call may be made on a stream that is capturing a
+ * CUDA graph.
  *
  *   row_ptr   int32[n + 1], device memory.
  *   arcs      device memory, 2 * m uint32 words: for arc e, arcs[2e] is the
@@ -270,7 +319,10 @@ SSSP_API int sssp_autotune(sssp_graph *g, const int32_t *srcs, int32_t nsrc, int
  *   dist_out  n elements, device memory; pred_out n int32, device memory or NULL.
  *   stream    cudaStream_t or NULL.
  * The CSR is validated on the device (SSSP_E_BADGRAPH).  Distances and
- * predecessors follow the conventions of sssp_solve.  SSSP_E_NOMEM if the
+ * predecessors follow the conventions of sssp_solve.  An fp32 weight of
+ * -0.0 is accepted and adds like +0.0, but the arcs are used as given (not
+ * normalised), so such an arc is routed like a weight above the light-arc
+ * bound; results are the same.  SSSP_E_NOMEM if the
  * fixed L2 rings overflow; host pointers are rejected with SSSP_E_INVAL. */
 SSSP_API int sssp_solve_noalloc(const int32_t *row_ptr, const uint32_t *arcs, int32_t n, int64_t m,
                                 int32_t wtype, int32_t src, void *dist_out, int32_t *pred_out,

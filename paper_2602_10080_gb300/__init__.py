@@ -47,7 +47,8 @@ class sssp_config(ctypes.Structure):
         ("filter_deltas", ctypes.c_float), ("near_deltas", ctypes.c_float), ("max_arcs", ctypes.c_int32),
         ("claim", ctypes.c_int32), ("shards", ctypes.c_int32), ("refillers", ctypes.c_int32),
         ("stage", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-        ("timeout_ms", ctypes.c_int32), ("l2_only", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+        ("timeout_ms", ctypes.c_int32), ("l2_only", ctypes.c_int32), ("split_arcs", ctypes.c_int32),
+        ("hub_bnum", ctypes.c_int32), ("dedup", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -98,12 +99,17 @@ class sssp_stats(ctypes.Structure):
         ("far_pushes", ctypes.c_int64), ("cas_fail", ctypes.c_int64), ("refills", ctypes.c_int64),
         ("deferred", ctypes.c_int64), ("relax_shadow", ctypes.c_int64), ("cycles", ctypes.c_int64 * 6),
         ("grid_blocks", ctypes.c_int32),
-        ("block_threads", ctypes.c_int32), ("attempts", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32), ("attempts", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("dup_targets", ctypes.c_int64), ("rounds", ctypes.c_int64), ("refill_tries", ctypes.c_int64),
+        ("wait_spins", ctypes.c_int64), ("idle_iters", ctypes.c_int64), ("window_pull_backs", ctypes.c_int64),
+        ("window_advances", ctypes.c_int64), ("lock_spins", ctypes.c_int64),
+        ("cycles_fine", ctypes.c_int64 * 3),
     ]
 
     def as_dict(self) -> dict:
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "cycles"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("cycles", "pad0", "cycles_fine")}
         d["cycles"] = dict(zip(self.CYCLE_NAMES, list(self.cycles)))
+        d["cycles_fine"] = dict(zip(("rounds", "push", "batch"), list(self.cycles_fine)))
         return d
 
 
@@ -138,6 +144,7 @@ def lib():
                                               ctypes.POINTER(I32)]),
         "sssp_last_stats": (ctypes.c_int, [P, ctypes.POINTER(sssp_stats)]),
         "sssp_autotune": (ctypes.c_int, [P, P, I32, I32, ctypes.POINTER(sssp_config)]),
+        "sssp_autotune_batch": (ctypes.c_int, [P, P, I32, I32, ctypes.POINTER(sssp_config)]),
         "sssp_serve_options_default": (ctypes.c_int, [ctypes.POINTER(sssp_serve_options)]),
         "sssp_serve_create": (ctypes.c_int, [ctypes.POINTER(sssp_serve_options), ctypes.POINTER(P)]),
         "sssp_serve_submit": (ctypes.c_int, [P, P, I32, P, P, ctypes.POINTER(ctypes.c_uint64)]),
@@ -240,6 +247,15 @@ def sssp_autotune(h, srcs=None, budget_ms: int = 0) -> sssp_config:
     c = sssp_config()
     nsrc = 0 if srcs is None else int(srcs.numel() if hasattr(srcs, "numel") else srcs.size)
     _check(lib().sssp_autotune(h, _ptr(srcs), nsrc, int(budget_ms), ctypes.byref(c)), "sssp_autotune")
+    return c
+
+
+def sssp_autotune_batch(h, srcs, budget_ms: int = 0) -> sssp_config:
+    """Tunes (and caches on the graph) the configuration of multi-query
+    launches of len(srcs) queries."""
+    c = sssp_config()
+    nq = int(srcs.numel() if hasattr(srcs, "numel") else srcs.size)
+    _check(lib().sssp_autotune_batch(h, _ptr(srcs), nq, int(budget_ms), ctypes.byref(c)), "sssp_autotune_batch")
     return c
 
 
@@ -374,3 +390,6 @@ class Graph:
 
     def autotune(self, srcs=None, budget_ms: int = 0) -> sssp_config:
         return sssp_autotune(self.handle, srcs, budget_ms)
+
+    def autotune_batch(self, srcs, budget_ms: int = 0) -> sssp_config:
+        return sssp_autotune_batch(self.handle, srcs, budget_ms)

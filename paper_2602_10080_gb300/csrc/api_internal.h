@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "../../include/sssp.h"
 #include "internal.h"
@@ -47,6 +48,7 @@ struct Graph {
     int32_t nv = 0;               // vertices of the device layout (real + shadow)
     int64_t mv = 0;               // arcs of the device layout
     int32_t split = 0;            // arcs per shadow vertex (0 = none split)
+    int32_t layout_req = 0;       // split threshold the current layout was built for
     int32_t wtype = 0;
     int32_t* row_ptr = nullptr;   // [nv + 1]
     uint2* adj = nullptr;         // [mv] (col, weight bits)
@@ -55,6 +57,13 @@ struct Graph {
     sssp_config defaults{};
     sssp_config tuned{};
     bool tuned_valid = false;
+    // multi-query configurations from sssp_autotune_batch, per size class
+    // (the number of queries rounded down to a power of two)
+    struct BatchTuned {
+        int32_t nq_class;
+        sssp_config cfg;
+    };
+    std::vector<BatchTuned> batch_tuned;
     sssp_stats last{};
     Workspace ws;
     std::mutex mu;
@@ -72,7 +81,15 @@ struct LaunchPlan {
     KParams P;
 };
 
+constexpr int32_t kDefaultSplit = 1024;   // default hub split threshold (sssp_config.split_arcs = 0)
+
 int cuda_status(cudaError_t e);
+// Serving lanes per graph uid: adds delta and returns the new count.  A
+// graph whose layout is in use by a lane is not relaid out.
+int lane_refs(uint64_t uid, int delta);
+// Makes the graph's layout the one for hub split threshold `split` (caller
+// holds g->mu); SSSP_E_BUSY while a serving lane uses the graph.
+int ensure_layout(Graph* g, int32_t split, cudaStream_t s);
 sssp_config prior_config(const Graph* g);   // the feature prior (sssp_autotune.cu)
 int pred_mode_for(const Graph* g);
 int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, LaunchPlan* out,
@@ -80,6 +97,12 @@ int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, 
 bool is_device_ptr(const void* p);
 void resolve_auto(const Graph* g, sssp_config* c);
 void batch_delta(const Graph* g, sssp_config* c, int div);   // delta / div for multi-query launches
+// Size class of a multi-query launch (nq rounded down to a power of two).
+int32_t nq_class(int32_t nq);
+// The batch-tuned configuration for nq queries (same size class), or null.
+const sssp_config* batch_tuned_for(const Graph* g, int32_t nq);
+// The batch-tuned configuration of the largest size class, or null (serving lanes).
+const sssp_config* batch_tuned_largest(const Graph* g);
 int validate_config(const sssp_config* c);
 // Run-time sampling request (sssp_solve_sampled): host output of cap
 // samples of kTimelineFields words, the period, and the count taken.

@@ -88,8 +88,14 @@ enum : int {
     kCyRelax, kCyL1, kCyL2Write, kCyGlobalRead, kCyIdle, kCyL0,
     kStLockSpin, kStWaitSpin, kStIdleIter, kStRefillTry, kStIter, kStRounds,
     kStPullBack, kStLowWrite, kStAdvance,
+    kStDup,           // improved arcs of a round whose target another improved arc of the round shares
+    kCyRound,         // SSSP_FINE_CYCLES: loads and relaxation of the rounds
+    kCyPush,          // SSSP_FINE_CYCLES: push_round (routing to L0 / far staging, their flushes)
+    kCyBatch,         // SSSP_FINE_CYCLES: batch set-up (stale filter, row offsets, prefix sum)
     kStCount
 };
+
+static_assert(kStCount <= 40, "Ctrl::stats holds 40 counters");
 
 struct __align__(128) Ctrl {
     unsigned long long reserve;          // elements ever written to L2
@@ -105,7 +111,7 @@ struct __align__(128) Ctrl {
     unsigned long long slice_end;        // serving: globaltimer value at which the current slice ends (0 = unset)
     unsigned long long processed;        // run-time sampling: elements taken for relaxation
     int pad3[24];
-    unsigned long long stats[32];
+    unsigned long long stats[40];
 };
 
 // The L2 rings: ring r = bucket * shards + shard uses rt[r * 32], wt[r * 32]
@@ -146,6 +152,10 @@ struct KParams {
     int32_t stage;           // 1: heavy-arc writes are pooled per bucket in the block before L2
     int32_t l2_only;         // 1: single-queue baseline (every write to L2, one chunk per read)
     int32_t unit_w;          // 1: breadth-first search: every real arc weighs 1, a shadow link 0
+    int32_t hub_bnum;        // > 0: shadow vertices (hub slices) use their own rings (the upper half
+                             // of each bucket's shards) and are read only from the first hub_bnum
+                             // non-empty buckets; 0: they share the rings
+    int32_t dedup;           // 1: one write per improved target of a warp round
     int32_t scratch_off, far_off, stat_off, stage_off, l1_off;  // byte offsets in dynamic shared memory
     unsigned long long timeout_ns;
     unsigned long long slice_ns;   // serving: end the launch after this long, draining local queues to L2 (0 = run to completion)
@@ -215,9 +225,89 @@ __device__ __forceinline__ uint2 vld(const volatile uint2* p) {
 // in which the two relaxed loads were performed.
 __device__ __forceinline__ bool ahead(uint32_t w, uint32_t r) { return (int32_t)(w - r) > 0; }
 
+// L2 residency.  The adjacency (8 bytes per arc) is streamed once per
+// expansion and is far larger than L2; the distance words, row offsets and
+// queue chunks are the reused working set.  With SSSP_L2_HINTS the arc loads
+// carry an evict-first L2 policy (and skip L1), and the distance loads, the
+// distance atomics and the row-offset loads an evict-last one, so the stream
+// does not push the working set out of L2.
+#ifndef SSSP_L2_HINTS
+#define SSSP_L2_HINTS 0
+#endif
+#ifndef SSSP_FINE_CYCLES
+#define SSSP_FINE_CYCLES 0
+#endif
+#ifndef SSSP_SPEC_ROW
+#define SSSP_SPEC_ROW 0
+#endif
+#ifndef SSSP_PIPELINE
+#define SSSP_PIPELINE 0
+#endif
+__device__ __forceinline__ unsigned long long pol_stream() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long pol_keep() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// one arc (column, weight bits); the graph is read-only during a solve
+__device__ __forceinline__ uint2 ld_arc(const uint2* p) {
+#if SSSP_L2_HINTS
+    uint2 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(r.x), "=r"(r.y) : "l"(p), "l"(pol_stream()));
+    return r;
+#else
+    return __ldg(p);
+#endif
+}
+// a row offset
+__device__ __forceinline__ int32_t ld_row(const int32_t* p) {
+#if SSSP_L2_HINTS
+    int32_t r;
+    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol_keep()));
+    return r;
+#else
+    return __ldg(p);
+#endif
+}
 // L2 load of a distance word (bypasses L1 so the filter sees recent values)
-__device__ __forceinline__ uint32_t ld_dist(const uint32_t* p) { return __ldcg(p); }
-__device__ __forceinline__ unsigned long long ld_dist(const unsigned long long* p) { return __ldcg(p); }
+__device__ __forceinline__ uint32_t ld_dist(const uint32_t* p) {
+#if SSSP_L2_HINTS
+    uint32_t r;
+    asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol_keep()));
+    return r;
+#else
+    return __ldcg(p);
+#endif
+}
+__device__ __forceinline__ unsigned long long ld_dist(const unsigned long long* p) {
+#if SSSP_L2_HINTS
+    unsigned long long r;
+    asm volatile("ld.global.cg.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol_keep()));
+    return r;
+#else
+    return __ldcg(p);
+#endif
+}
+// distance minimum whose old value is not needed (a reduction)
+__device__ __forceinline__ void red_min(uint32_t* p, uint32_t v) {
+#if SSSP_L2_HINTS
+    asm volatile("red.relaxed.gpu.global.min.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol_keep()));
+#else
+    atomicMin(p, v);
+#endif
+}
+__device__ __forceinline__ void red_min(unsigned long long* p, unsigned long long v) {
+#if SSSP_L2_HINTS
+    asm volatile("red.relaxed.gpu.global.min.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol_keep()));
+#else
+    atomicMin(p, v);
+#endif
+}
 
 // ------------------------------------------------------------ arithmetic --
 
@@ -290,6 +380,20 @@ __device__ __forceinline__ void raise_error(Ctrl* C, int code, int where, int in
         C->err_info = info;
     }
     __threadfence();
+}
+
+// Release/acquire fence at GPU scope between a warp's queue writes and the
+// word that publishes them (chunk sequence numbers, the block count, done).
+// SSSP_FENCE_SC=1 uses the sequentially consistent __threadfence instead.
+#ifndef SSSP_FENCE_SC
+#define SSSP_FENCE_SC 1
+#endif
+__device__ __forceinline__ void fence_gpu() {
+#if SSSP_FENCE_SC
+    __threadfence();
+#else
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+#endif
 }
 
 // ---------------------------------------------------------------- kernel --
@@ -400,7 +504,7 @@ struct Worker {
         while ((uint32_t)(v >> 32) == 0u && (uint32_t)v != 0u) {
             unsigned long long old = atomicCAS(&S()->acct, v, 0ull);
             if (old == v) {
-                __threadfence();
+                fence_gpu();
                 atomicAdd(&P.ctrl->done, (unsigned long long)(uint32_t)v);
                 return;
             }
@@ -413,7 +517,7 @@ struct Worker {
         unc = 0;
         dec = 0;
         if (lane == 0 && delta != 0) {
-            __threadfence();
+            fence_gpu();
             unsigned long long add = ((unsigned long long)(uint32_t)delta) << 32;
             unsigned long long old = atomicAdd(&S()->acct, add);
             if ((uint32_t)(old >> 32) + (uint32_t)delta == 0u) try_flush();
@@ -466,6 +570,17 @@ struct Worker {
     __device__ __forceinline__ uint32_t home_shard() const {
         return (blockIdx.x + (threadIdx.x >> 5)) & (uint32_t)(P.shards - 1);
     }
+    // The shard an element is written to: its home shard, or with hub rings
+    // (hub_bnum > 0) the lower half of the shards for ordinary vertices and
+    // the upper half for shadow vertices.
+    __device__ __forceinline__ uint32_t write_shard(bool shadow) const {
+        if (P.hub_bnum <= 0) return home_shard();
+        const uint32_t half = (uint32_t)P.shards >> 1;
+        return (shadow ? half : 0u) + (home_shard() & (half - 1u));
+    }
+    __device__ __forceinline__ bool hub_ring(uint32_t shard) const {
+        return P.hub_bnum > 0 && shard >= ((uint32_t)P.shards >> 1);
+    }
 
     // Serving: adds `sign` per valid element to its query's L2 count, one
     // atomic per distinct query of the warp.  At the end of a slice every
@@ -499,13 +614,13 @@ struct Worker {
         }
         win = __shfl_sync(kFull, win, 0);
         const uint32_t W = (uint32_t)win;
-        const uint32_t shard = home_shard();
         // absolute bucket (clamp_bucket: beyond the window's reach -> its far end)
         uint32_t ab = valid ? abs_bucket(e.x, e.y) : W;
         ab = clamp_bucket(ab, W);
         const uint32_t b = ab % (uint32_t)P.bmax;
         const uint32_t below = __reduce_min_sync(kFull, valid ? ab : 0xffffffffu);
         const bool shadow = valid && key_vertex(e.x) >= (uint32_t)P.n;
+        const uint32_t shard = write_shard(shadow);
         const uint32_t gkey = !valid ? 0xffffffffu : (shadow ? (0x80000000u | lane) : b);
         const uint32_t grp = __match_any_sync(kFull, gkey);
         const bool leader = valid && (grp & lanemask_lt()) == 0u;
@@ -560,7 +675,7 @@ struct Worker {
         __syncwarp();
         if (leader) {
             P.l2.cnt[slot] = (uint32_t)__popc(grp);
-            __threadfence();
+            fence_gpu();
             st_release(P.l2.seq + slot, t + 1u);
         }
         stat(kStChunks, (unsigned long long)__popc(__ballot_sync(kFull, leader)));
@@ -577,16 +692,14 @@ struct Worker {
 
     // Probes the L2 rings of the window, lowest absolute bucket first: lane i
     // looks at absolute bucket W + round * (32 / S) + i / S, shard
-    // (home + i) % S.  When the lowest buckets are empty the window moves up
-    // to the lowest non-empty one ("base is increased by delta when the first
-    // bucket is empty", Section 4.2).  The window only moves forward: ring k
-    // serves buckets k, k + bmax, ..., so moving it back would let elements
-    // written to the far end of the window pass for the lowest buckets.
-    // Writers keep every element inside the window (clamp_bucket), and every
-    // ring lies inside it, so no element is left behind.  Claims up to `want`
-    // chunks of the lowest non-empty ring among the first bnum buckets with
-    // one CAS on its read ticket.  Returns the number of chunks claimed
-    // (warp-uniform) with their ring and first ticket.
+    // (home + i) % S.  When the lowest buckets are empty a reader moves the
+    // window up to the lowest non-empty one (the base advance of Section
+    // 4.2); a writer below the window pulls it back (l2_write).  Writers keep
+    // every element inside the window's reach (clamp_bucket), and every ring
+    // lies inside it, so no element is left behind.  Claims up to `want`
+    // chunks of the lowest non-empty ring among the first bnum buckets (hub
+    // rings: the first hub_bnum) with one CAS on its read ticket.  Returns the
+    // number of chunks claimed (warp-uniform) with their ring and first ticket.
     __device__ uint32_t l2_claim(uint32_t want, uint32_t& ring_out, uint32_t& t_out) {
         unsigned long long win = 0;
         if (lane == 0) win = window();
@@ -610,8 +723,12 @@ struct Worker {
             const uint32_t first_rel = r0 + (uint32_t)first / S_;
             if (first_rel > 0 && lane == 0)
                 if (atomicCAS(&P.ctrl->window, win, (unsigned long long)(W + first_rel)) == win) sst()[kStAdvance]++;
-            // candidates: non-empty rings of buckets within bnum of the first one
-            uint32_t cand = __ballot_sync(kFull, ne && rel < first_rel + (uint32_t)P.bnum);
+            // candidates: non-empty rings of buckets within bnum of the first
+            // one; hub rings only within hub_bnum of it (a hub slice is
+            // relaxed once its distance is near the front, so it is rarely
+            // relaxed again)
+            const uint32_t lim = hub_ring((home + lane) & (S_ - 1u)) ? (uint32_t)P.hub_bnum : (uint32_t)P.bnum;
+            uint32_t cand = __ballot_sync(kFull, ne && rel < first_rel + lim);
             while (cand) {
                 int c = __ffs(cand) - 1;
                 uint32_t got = 0, t = 0;
@@ -674,7 +791,7 @@ struct Worker {
         count_live(valid, e.x, -1);
         __syncwarp();
         if (lane == 0) {
-            __threadfence();
+            fence_gpu();
             st_release(P.l2.seq + slot, tj + P.l2.nch);
         }
         __syncwarp();
@@ -1117,8 +1234,8 @@ struct Worker {
             if (r == (uint32_t)i) l0[i] = x;
     }
 
-    // L0 is full: write all of it to L1 (Section 3.4: "when the L0 queue is
-    // full, all its elements are transferred to the L1 queue").
+    // L0 is full: its whole content moves down to L1 (the L0 overflow rule of
+    // Section 3.4).
     __device__ void l0_spill() {
         uint2 e[R];
         bool v[R];
@@ -1354,12 +1471,12 @@ struct Worker {
         nd = A::add(du, wbits);
         if (PRED == 0) {
             if (nd >= (uint32_t)cur) return false;
-            atomicMin(reinterpret_cast<uint32_t*>(dist()) + vidx, nd);
+            red_min(reinterpret_cast<uint32_t*>(dist()) + vidx, nd);
             return true;
         } else if (PRED == 1) {
             const unsigned long long cand = ((unsigned long long)nd << 32) | u;
             if (cand >= (unsigned long long)cur) return false;
-            atomicMin(reinterpret_cast<unsigned long long*>(dist()) + vidx, cand);
+            red_min(reinterpret_cast<unsigned long long*>(dist()) + vidx, cand);
             return (uint32_t)((unsigned long long)cur >> 32) > nd;
         } else {
             unsigned long long* p = reinterpret_cast<unsigned long long*>(dist()) + vidx;
@@ -1383,6 +1500,24 @@ struct Worker {
     // the current bucket only).  With admission offsets (serving) front is a
     // bucket, otherwise a distance.
     __device__ __forceinline__ void push_round(bool imp, uint32_t key, uint32_t nd, uint32_t w, uint32_t front) {
+        stat(kStImproved, (unsigned long long)(__popc(__ballot_sync(kFull, imp))));
+        if (P.dedup) {
+            // in-warp duplicates (Listing 1's write of a warp's improved
+            // vertices): lanes whose arcs improved the same target this round
+            // are matched; one write per target is enough, the one with the
+            // smallest distance (ties: lowest lane) -- the others carry larger
+            // or equal distances and would be dropped as stale when read
+            const unsigned long long mk = imp ? (unsigned long long)key : (0x100000000ull | lane);
+            const uint32_t grp = __match_any_sync(kFull, mk);
+            const bool dup = imp && (grp & (grp - 1u)) != 0u;
+            const uint32_t dm = __ballot_sync(kFull, dup);
+            if (dm) {
+                stat(kStDup, (unsigned long long)__popc(dm));
+                const uint32_t mn = __reduce_min_sync(grp, imp ? nd : 0xffffffffu);
+                const uint32_t at_min = __ballot_sync(kFull, imp && nd == mn) & grp;
+                if (dup && lane != (uint32_t)(__ffs(at_min) - 1)) imp = false;
+            }
+        }
         // a shadow vertex (a slice of a hub's arcs) always goes to L2 so that
         // the slices of one hub spread over all blocks
         const bool inside = MQ && P.qoff ? abs_bucket(key, nd) <= front : nd <= front;
@@ -1394,7 +1529,6 @@ struct Worker {
             l0_push(__popc(m));
         }
         far_push(imp && !nearv, make_uint2(key, nd));
-        stat(kStImproved, (unsigned long long)(__popc(__ballot_sync(kFull, imp))));
     }
 
     // One lane's arc of a relaxation round: the adjacency entry (col,
@@ -1423,7 +1557,7 @@ struct Worker {
         r.q = MQ ? __shfl_sync(kFull, myq, j) : 0u;
         r.pu = PRED != 0 ? __shfl_sync(kFull, pu, j) : 0u;
         r.in = g < total;
-        r.a = r.in ? __ldg(P.adj + (ors + (g - oex))) : make_uint2(0u, 0u);
+        r.a = r.in ? ld_arc(P.adj + (ors + (g - oex))) : make_uint2(0u, 0u);
         if (P.unit_w) r.a.y = r.a.x >= (uint32_t)P.n ? 0u : 1u;
         return r;
     }
@@ -1436,6 +1570,9 @@ struct Worker {
     // max_arcs go back to L0 for the next batch.  Returns the number of
     // elements consumed.
     __device__ int relax_batch(bool valid, uint2 el) {
+#if SSSP_FINE_CYCLES
+        const long long cb0 = clock64();
+#endif
         uint32_t key = el.x, du = el.y;
         int32_t rs = 0, deg = 0;
         bool stale = false;
@@ -1444,15 +1581,30 @@ struct Worker {
             valid = false;
         }
         if (valid) {
+#if SSSP_SPEC_ROW
+            // the row offsets are loaded alongside the distance (one memory
+            // round trip instead of two); a stale vertex ignores them
+            const uint32_t v = key_vertex(key);
+            const uint32_t cur = dpart(ld_dist(dist() + dist_index(key)));
+            const int32_t r0 = ld_row(P.row_ptr + v), r1 = ld_row(P.row_ptr + v + 1);
+            if (du > cur) {
+                valid = false;
+                stale = true;
+            } else {
+                rs = r0;
+                deg = r1 - r0;
+            }
+#else
             uint32_t cur = dpart(ld_dist(dist() + dist_index(key)));
             if (du > cur) {
                 valid = false;
                 stale = true;
             } else {
                 uint32_t v = key_vertex(key);
-                rs = __ldg(P.row_ptr + v);
-                deg = __ldg(P.row_ptr + v + 1) - rs;
+                rs = ld_row(P.row_ptr + v);
+                deg = ld_row(P.row_ptr + v + 1) - rs;
             }
+#endif
         }
         int consumed = __popc(__ballot_sync(kFull, valid || stale));
         stat(kStStale, (unsigned long long)(__popc(__ballot_sync(kFull, stale))));
@@ -1503,11 +1655,18 @@ struct Worker {
             pu = v < (uint32_t)P.n ? v : (uint32_t)__ldg(P.owner + (v - (uint32_t)P.n));
         }
         stat(kStRelax, (unsigned long long)((uint32_t)total));
+#if SSSP_FINE_CYCLES
+        stat(kCyBatch, (unsigned long long)(clock64() - cb0));
+#endif
         {
             const int32_t sh = valid && key_vertex(key) >= (uint32_t)P.n ? deg : 0;
             const int32_t shs = __reduce_add_sync(kFull, (uint32_t)sh);
             if (shs) stat(kStRelaxShadow, (unsigned long long)shs);
         }
+#if SSSP_PIPELINE
+        // the next round's arcs are loaded while this round's distances are
+        RoundIn nx = round_in(0, total, ex, rs, du, myq, pu);
+#endif
         for (int32_t g0 = 0; g0 < total; g0 += 32) {
             if (g0 && (g0 & 4095) == 0) {
                 int stop = 0;
@@ -1515,14 +1674,29 @@ struct Worker {
                 if (__shfl_sync(kFull, stop, 0)) break;
             }
             stat(kStRounds, 1);
+#if SSSP_FINE_CYCLES
+            const long long cr0 = clock64();
+#endif
+#if SSSP_PIPELINE
+            const RoundIn cu = nx;
+            if (g0 + 32 < total) nx = round_in(g0 + 32, total, ex, rs, du, myq, pu);
+#else
             const RoundIn cu = round_in(g0, total, ex, rs, du, myq, pu);
+#endif
             uint32_t nd = 0;
             bool imp = false;
             if (cu.in) {
                 const size_t vidx = MQ ? (size_t)cu.q * (size_t)P.nv + cu.a.x : (size_t)cu.a.x;
                 imp = relax_cur(vidx, cu.pu, cu.du, cu.a.y, ld_dist(dist() + vidx), nd);
             }
+#if SSSP_FINE_CYCLES
+            const long long cr1 = clock64();
+            stat(kCyRound, (unsigned long long)__shfl_sync(kFull, (unsigned long long)(cr1 - cr0), 0));
+#endif
             push_round(imp, MQ ? ((cu.q << P.vbits) | cu.a.x) : cu.a.x, nd, cu.a.y, front);
+#if SSSP_FINE_CYCLES
+            stat(kCyPush, (unsigned long long)(clock64() - cr1));
+#endif
         }
         return consumed;
     }

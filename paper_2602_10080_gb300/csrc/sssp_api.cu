@@ -115,9 +115,9 @@ __global__ void ring_reset_kernel(Rings r, uint32_t nrings, Ctrl* ctrl) {
     }
 }
 
-// Resets the control block and writes the sources through to the current
-// L2 bucket (Section 4.1: "the source vertex is first written through to
-// the L2 queue"), reserve = number of queries.  One warp.
+// Resets the control block and puts the sources straight into the current
+// L2 bucket, as the start-up of Section 4.1 does; reserve = number of
+// queries.  One warp.
 __global__ void seed_kernel(KParams P, const int32_t* srcs, int32_t src0, int32_t nq, int packed) {
     Ctrl* C = P.ctrl;
     const uint32_t lane = threadIdx.x & 31u;
@@ -130,7 +130,7 @@ __global__ void seed_kernel(KParams P, const int32_t* srcs, int32_t src0, int32_
         C->error = 0;
         C->err_where = 0;
         C->err_info = 0;
-        for (int i = 0; i < 32; i++) C->stats[i] = 0;
+        for (int i = 0; i < kStCount; i++) C->stats[i] = 0;
         C->window = 0;  // sources sit in absolute bucket 0
         cur_s = 0;
     }
@@ -416,6 +416,9 @@ static void config_defaults(sssp_config* c) {
     c->block_threads = 512;
     c->blocks_per_sm = 0;
     c->timeout_ms = 0;
+    c->split_arcs = 0;
+    c->hub_bnum = 0;
+    c->dedup = 0;
 }
 
 // Fills auto fields from the graph features (the prior of Section 3.5).
@@ -453,6 +456,26 @@ void batch_delta(const Graph* g, sssp_config* c, int div) {
     else c->delta_u32 = std::max<uint32_t>(1u, c->delta_u32 / (uint32_t)div);
 }
 
+int32_t nq_class(int32_t nq) {
+    int32_t c = 1;
+    while (c <= nq / 2) c *= 2;
+    return c;
+}
+
+const sssp_config* batch_tuned_for(const Graph* g, int32_t nq) {
+    const int32_t k = nq_class(nq);
+    for (const Graph::BatchTuned& b : g->batch_tuned)
+        if (b.nq_class == k) return &b.cfg;
+    return nullptr;
+}
+
+const sssp_config* batch_tuned_largest(const Graph* g) {
+    const Graph::BatchTuned* best = nullptr;
+    for (const Graph::BatchTuned& b : g->batch_tuned)
+        if (!best || b.nq_class > best->nq_class) best = &b;
+    return best ? &best->cfg : nullptr;
+}
+
 int validate_config(const sssp_config* c) {
     auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
     if (c->l1_type < 0 || c->l1_type > 3) return SSSP_E_INVAL;
@@ -470,8 +493,9 @@ int validate_config(const sssp_config* c) {
     if (c->blocks_per_sm < 0 || c->blocks_per_sm > 8 || c->timeout_ms < 0) return SSSP_E_INVAL;
     if (c->stage < 0 || c->stage > 1) return SSSP_E_INVAL;
     if (c->l2_only < 0 || c->l2_only > 1) return SSSP_E_INVAL;
-    for (int i = 0; i < 2; i++)
-        if (c->reserved[i] != 0) return SSSP_E_INVAL;
+    if (c->split_arcs != 0 && (c->split_arcs < 32 || c->split_arcs > (1 << 30))) return SSSP_E_INVAL;
+    if (c->hub_bnum < 0 || c->hub_bnum > 32 || c->dedup < 0 || c->dedup > 1) return SSSP_E_INVAL;
+    if (c->reserved != 0) return SSSP_E_INVAL;
     return SSSP_OK;
 }
 
@@ -515,6 +539,9 @@ int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, 
     P.shards = cfg.shards;
     P.delta = f32 ? __float_as_uint_host(cfg.delta_f32) : cfg.delta_u32;
     P.unit_w = unit ? 1 : 0;
+    // hub rings need two shard halves and a bucketed L2
+    P.hub_bnum = (cfg.shards >= 2 && cfg.bmax > 1 && !cfg.l2_only) ? cfg.hub_bnum : 0;
+    P.dedup = cfg.dedup;
     P.bnum = std::min(cfg.bnum, cfg.bmax);
     P.bmax = cfg.bmax;
     P.l1_type = cfg.l1_type;
@@ -550,6 +577,9 @@ int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, 
 int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int32_t src0, int32_t nq,
                 void* dist_out, int32_t* pred_out, const sssp_config* cfg_in, cudaStream_t stream,
                 sssp_stats* st_out, bool unit, const Sampling* samp) {
+    // a multi-query launch with the library's configuration uses the
+    // batch-tuned one of its size class when sssp_autotune_batch made one
+    if (!cfg_in && nq > 1 && !unit) cfg_in = batch_tuned_for(g, nq);
     sssp_config cfg = cfg_in ? *cfg_in : (g->tuned_valid ? g->tuned : g->defaults);
     // breadth-first: one bucket per level unless the caller chose a delta
     if (unit && (!cfg_in || cfg.delta_u32 == 0)) cfg.delta_u32 = 1;
@@ -562,6 +592,8 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
     int rc = validate_config(&cfg);
     if (rc) return rc;
     if (cudaSetDevice(g->device) != cudaSuccess) return SSSP_E_CUDA;
+    rc = ensure_layout(g, cfg.split_arcs ? cfg.split_arcs : kDefaultSplit, stream);
+    if (rc) return rc;
     const int32_t n = g->n, nv = g->nv;
     const bool mq = nq > 1;
     int vbits = 0;
@@ -774,6 +806,17 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
         st.grid_blocks = grid;
         st.block_threads = threads;
         st.attempts = attempts;
+        st.dup_targets = (int64_t)hc.stats[kStDup];
+        st.rounds = (int64_t)hc.stats[kStRounds];
+        st.refill_tries = (int64_t)hc.stats[kStRefillTry];
+        st.wait_spins = (int64_t)hc.stats[kStWaitSpin];
+        st.idle_iters = (int64_t)hc.stats[kStIdleIter];
+        st.window_pull_backs = (int64_t)hc.stats[kStPullBack];
+        st.window_advances = (int64_t)hc.stats[kStAdvance];
+        st.lock_spins = (int64_t)hc.stats[kStLockSpin];
+        st.cycles_fine[0] = (int64_t)hc.stats[kCyRound];
+        st.cycles_fine[1] = (int64_t)hc.stats[kCyPush];
+        st.cycles_fine[2] = (int64_t)hc.stats[kCyBatch];
         g->last = st;
         if (st_out) *st_out = st;
         if (dbg > 1)
@@ -901,6 +944,126 @@ static int build_layout(Graph* g, int32_t* rp0, uint2* adj0, int32_t split, cuda
     return SSSP_OK;
 }
 
+// Original arc order from a shadow layout: the arcs of vertex v are its own
+// row, or (a split hub) the rows of its shadows, which are consecutive.  One
+// warp per vertex copies them to their place in the original CSR.
+__global__ void unsplit_kernel(const uint2* adj1, const int32_t* src_start, const int32_t* rp0, int32_t n,
+                               uint2* adj0) {
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    for (int64_t v = wid; v < n; v += nw) {
+        const int32_t b = rp0[v], e = rp0[v + 1], src = src_start[v];
+        for (int32_t i = (int32_t)lane; i < e - b; i += 32) adj0[b + i] = adj1[src + i];
+    }
+}
+
+int lane_refs(uint64_t uid, int delta) {
+    static std::mutex mu;
+    static std::vector<std::pair<uint64_t, int>> refs;
+    std::lock_guard<std::mutex> lk(mu);
+    for (size_t i = 0; i < refs.size(); i++) {
+        if (refs[i].first != uid) continue;
+        refs[i].second += delta;
+        const int c = refs[i].second;
+        if (c <= 0) refs.erase(refs.begin() + (long)i);
+        return c;
+    }
+    if (delta > 0) refs.emplace_back(uid, delta);
+    return delta > 0 ? delta : 0;
+}
+
+int ensure_layout(Graph* g, int32_t split, cudaStream_t s) {
+    if (split == g->layout_req) return SSSP_OK;
+    // no vertex is split under either threshold: the layout is the same
+    if (g->split == 0 && g->feat.max_deg <= (double)split) {
+        g->layout_req = split;
+        return SSSP_OK;
+    }
+    if (lane_refs(g->uid, 0) > 0) return SSSP_E_BUSY;
+    const int32_t n = g->n;
+    int32_t* rp0 = nullptr;
+    uint2* adj0 = nullptr;
+    int32_t* old_rp = g->row_ptr;
+    uint2* old_adj = g->adj;
+    int32_t* old_owner = g->owner;
+    if (g->split == 0) {
+        // the current layout is the original CSR: hand it over
+        rp0 = g->row_ptr;
+        adj0 = g->adj;
+    } else {
+        const int32_t nv = g->nv;
+        std::vector<int32_t> rp1((size_t)nv + 1), owner((size_t)(nv - n));
+        if (cudaMemcpyAsync(rp1.data(), g->row_ptr, sizeof(int32_t) * ((size_t)nv + 1), cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess ||
+            cudaMemcpyAsync(owner.data(), g->owner, sizeof(int32_t) * (size_t)(nv - n), cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return SSSP_E_CUDA;
+        std::vector<int32_t> first(n, -1), count(n, 0);
+        for (int32_t i = 0; i < nv - n; i++) {
+            const int32_t v = owner[(size_t)i];
+            if (first[v] < 0) first[v] = n + i;
+            count[v]++;
+        }
+        std::vector<int32_t> h0((size_t)n + 1), src((size_t)n);
+        int64_t pos = 0;
+        for (int32_t v = 0; v < n; v++) {
+            h0[v] = (int32_t)pos;
+            if (first[v] >= 0) {
+                src[v] = rp1[first[v]];
+                pos += rp1[first[v] + count[v]] - rp1[first[v]];
+            } else {
+                src[v] = rp1[v];
+                pos += rp1[v + 1] - rp1[v];
+            }
+        }
+        h0[n] = (int32_t)pos;
+        if (pos != g->m) return SSSP_E_BADGRAPH;
+        int32_t* d_src = nullptr;
+        if (cudaMalloc(&rp0, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
+            cudaMalloc(&adj0, sizeof(uint2) * std::max<size_t>((size_t)g->m, 1)) != cudaSuccess ||
+            cudaMalloc(&d_src, sizeof(int32_t) * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(rp0);
+            cudaFree(adj0);
+            cudaFree(d_src);
+            return SSSP_E_NOMEM;
+        }
+        cudaMemcpyAsync(rp0, h0.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_src, src.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s);
+        unsplit_kernel<<<g->sms * 8, 256, 0, s>>>(g->adj, d_src, rp0, n, adj0);
+        const cudaError_t e = cudaStreamSynchronize(s);
+        cudaFree(d_src);
+        if (e != cudaSuccess) {
+            cudaFree(rp0);
+            cudaFree(adj0);
+            return cuda_status(e);
+        }
+    }
+    // build_layout frees rp0/adj0 when it makes new arrays and keeps them
+    // as the layout otherwise; it leaves the graph untouched on failure
+    const bool handed = rp0 == old_rp;
+    const int rc = build_layout(g, rp0, adj0, split, s);
+    if (rc != SSSP_OK) {
+        if (!handed) {
+            cudaFree(rp0);
+            cudaFree(adj0);
+        }
+        return rc;
+    }
+    if (!handed) {
+        // the previous layout was split: its arrays are no longer used
+        cudaFree(old_rp);
+        cudaFree(old_adj);
+        cudaFree(old_owner);
+    }
+    g->layout_req = split;
+    g->feat.shadows = g->nv - g->n;
+    g->ws.dirty = true;
+    return SSSP_OK;
+}
+
 }  // namespace sssp
 
 // ==================================================================== C ABI
@@ -1009,7 +1172,8 @@ extern "C" int sssp_graph_create(const int32_t* row_ptr, const int32_t* col_idx,
         }
         f.symmetric = -1;
         f.has_zero_w = hacc.zero_w ? 1 : 0;
-        rc = build_layout(g, rp0, adj0, 1024, s);
+        rc = build_layout(g, rp0, adj0, kDefaultSplit, s);
+        g->layout_req = kDefaultSplit;
         f.shadows = g->nv - g->n;
         // the graph's default configuration: the feature prior (Section 3.5)
         g->defaults = prior_config(g);

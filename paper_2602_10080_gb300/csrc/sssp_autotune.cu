@@ -8,13 +8,20 @@
 //       bucket queue when large; meshes: L1FQ-L2V; power-law: priority-aware
 //       L1 over the bucket queue), and
 //   (2) a short timed coordinate search around the prior on sample sources:
-//       L1 policy, delta, near window, bnum, shards, claim size, batch size
-//       and block size, each
-//       candidate timed by the CUDA-event duration of the relaxation kernel.
+//       L1 policy, delta, near window, bnum, shards, claim size, batch size,
+//       block size, L1 depth, refill concurrency, hub split threshold and hub
+//       rings, each candidate timed by the CUDA-event duration of the
+//       relaxation kernel.
 // The winner is cached on the graph and used by solves given cfg == NULL.
+//
+// sssp_autotune_batch does the same for multi-query launches of a given size:
+// it times whole batch launches over the bucket-width divisor, bnum, L1
+// depth, claim size, refill concurrency and hub rings, and caches the winner
+// per size class for sssp_solve_batch and the serving lanes.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "../../include/sssp.h"
@@ -190,6 +197,32 @@ extern "C" int sssp_autotune(sssp_graph* gh, const int32_t* srcs, int32_t nsrc, 
             c.block_threads = bt;
             cands.push_back(c);
         }
+        // queue depth of L1, refill concurrency, and the hub handling: the
+        // split threshold ("threads per vertex" above which a vertex's arcs
+        // are spread over warps) and the hub rings
+        for (int l1 : {1024, 4096}) {
+            sssp_config c = best;
+            c.l1_cap = l1;
+            cands.push_back(c);
+        }
+        for (int rf : {4, 16}) {
+            sssp_config c = best;
+            c.refillers = rf;
+            cands.push_back(c);
+        }
+        for (int hb : {0, 1, 2}) {
+            sssp_config c = best;
+            if (c.hub_bnum == hb) continue;
+            c.hub_bnum = hb;
+            cands.push_back(c);
+        }
+        if (g->feat.max_deg > 256.0) {
+            for (int sp : {256, 4096}) {
+                sssp_config c = best;
+                c.split_arcs = sp;
+                cands.push_back(c);
+            }
+        }
         for (const sssp_config& c : cands) {
             if (elapsed_ms() > budget_ms) break;
             if (validate_config(&c) != SSSP_OK) continue;
@@ -203,6 +236,108 @@ extern "C" int sssp_autotune(sssp_graph* gh, const int32_t* srcs, int32_t nsrc, 
     cudaFree(dbuf);
     g->tuned = best;
     g->tuned_valid = true;
+    if (out) *out = best;
+    return SSSP_OK;
+}
+
+extern "C" int sssp_autotune_batch(sssp_graph* gh, const int32_t* srcs, int32_t nq, int32_t budget_ms,
+                                   sssp_config* out) {
+    if (!gh || !srcs || nq < 2 || budget_ms < 0) return SSSP_E_INVAL;
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    std::lock_guard<std::mutex> lk(g->mu);
+    std::vector<int32_t> hs(nq);
+    if (is_device_ptr(srcs)) {
+        if (cudaMemcpy(hs.data(), srcs, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return SSSP_E_CUDA;
+    } else {
+        hs.assign(srcs, srcs + nq);
+    }
+    for (int32_t s : hs)
+        if (s < 0 || s >= g->n) return SSSP_E_INVAL;
+    // the starting point: the graph's configuration with the library's
+    // multi-query bucket width (the heuristic sssp_solve_batch uses untuned)
+    sssp_config base = g->tuned_valid ? g->tuned : g->defaults;
+    base.delta_u32 = 0;
+    base.delta_f32 = 0.0f;
+    resolve_auto(g, &base);
+    const int div0 = std::min(16, std::max(1, nq / 32));
+    batch_delta(g, &base, div0);
+    base.bnum = std::min(base.bnum, 4);
+    sssp_config best = base;
+    if (budget_ms > 0) {
+        void* dbuf = nullptr;
+        if (cudaMalloc(&dbuf, sizeof(uint32_t) * (size_t)g->n * (size_t)nq) != cudaSuccess) {
+            cudaGetLastError();
+            return SSSP_E_NOMEM;
+        }
+        const auto t0 = std::chrono::steady_clock::now();
+        auto elapsed_ms = [&]() {
+            return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        };
+        auto measure = [&](const sssp_config& c) -> double {
+            sssp_stats st;
+            int rc = run_queries(g, hs.data(), nullptr, 0, nq, dbuf, nullptr, &c, nullptr, &st);
+            return rc == SSSP_OK ? st.kernel_ms : INFINITY;
+        };
+        measure(best);   // warm-up (allocations, first launch)
+        double best_t = measure(best);
+        const bool f32 = g->wtype == SSSP_W_F32;
+        sssp_config general = base;
+        batch_delta(g, &general, 1);
+        const double d1 = f32 ? general.delta_f32 : (double)general.delta_u32;
+        for (int pass = 0; pass < 2 && elapsed_ms() < budget_ms; pass++) {
+            std::vector<sssp_config> cands;
+            for (int div : {2, 4, 8, 16, 32}) {
+                sssp_config c = best;
+                if (f32) c.delta_f32 = (float)(d1 / div);
+                else c.delta_u32 = (uint32_t)std::max(1.0, std::floor(d1 / div));
+                cands.push_back(c);
+            }
+            for (int bn : {1, 2, 4, 8}) {
+                sssp_config c = best;
+                c.bnum = bn;
+                cands.push_back(c);
+            }
+            for (int l1 : {1024, 2048, 4096}) {
+                sssp_config c = best;
+                c.l1_cap = l1;
+                cands.push_back(c);
+            }
+            for (int cl : {2, 4, 8}) {
+                sssp_config c = best;
+                c.claim = cl;
+                cands.push_back(c);
+            }
+            for (int rf : {4, 8, 16}) {
+                sssp_config c = best;
+                c.refillers = rf;
+                cands.push_back(c);
+            }
+            for (int hb : {0, 1, 2}) {
+                sssp_config c = best;
+                c.hub_bnum = hb;
+                cands.push_back(c);
+            }
+            for (const sssp_config& c : cands) {
+                if (elapsed_ms() > budget_ms) break;
+                if (std::memcmp(&c, &best, sizeof(c)) == 0 || validate_config(&c) != SSSP_OK) continue;
+                const double t = measure(c);
+                if (t < best_t * 0.97) {
+                    best_t = t;
+                    best = c;
+                }
+            }
+        }
+        cudaFree(dbuf);
+    }
+    const int32_t k = nq_class(nq);
+    bool found = false;
+    for (Graph::BatchTuned& b : g->batch_tuned)
+        if (b.nq_class == k) {
+            b.cfg = best;
+            found = true;
+        }
+    if (!found) g->batch_tuned.push_back(Graph::BatchTuned{k, best});
     if (out) *out = best;
     return SSSP_OK;
 }

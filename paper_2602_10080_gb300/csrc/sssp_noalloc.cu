@@ -14,13 +14,14 @@
 // library holds it (kNoAllocBytes, about 25 MiB) until the process exits.
 // Host code cannot use the array's name as a device address, so the first
 // call on each device resolves it with cudaGetSymbolAddress (with that device
-// current) and resets the queue metadata; that first call should therefore
-// come before any stream capture.  All calls share the array and it keeps
-// the previous call's contents: each call re-initialises what must start
-// empty (control block, distance words), and the rings are left empty by a
-// successful solve and reset after a failed one.  Calls that overlap on the
-// GPU would race on the array; this file serialises the calls it issues with
-// a process-wide mutex and returns only after the GPU work has finished.
+// current).  All calls share the array and it keeps the previous call's
+// contents: every call first re-initialises what must start empty (the
+// queue metadata and control block, then the distance words), so no call
+// depends on how the previous one ended.  Calls that overlap on the GPU
+// would race on the array; this file serialises the calls it issues with a
+// process-wide mutex and returns only after the GPU work has finished.  A
+// call reads results back and synchronises its stream part-way, so it must
+// not be issued on a stream that is being captured into a CUDA graph.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -185,9 +186,6 @@ extern "C" int sssp_solve_noalloc(const int32_t* row_ptr, const uint32_t* arcs, 
             return SSSP_E_CUDA;
         }
         D.base = static_cast<unsigned char*>(ptr);
-        NaLayout L0 = na_layout(D.base);
-        ring_reset_kernel<<<std::max(1, sms * 4), 256, 0, stream>>>(L0.rings, kNaBuckets, L0.ctrl);
-        if (cudaStreamSynchronize(stream) != cudaSuccess) return SSSP_E_CUDA;
         D.ready = true;
     }
     NaLayout L = na_layout(D.base);
@@ -265,6 +263,8 @@ extern "C" int sssp_solve_noalloc(const int32_t* row_ptr, const uint32_t* arcs, 
     P.timeout_ns = 20000ull * 1000000ull;
 
     const size_t cells = (size_t)n;
+    // empty queue metadata and control block, whatever the previous call left
+    ring_reset_kernel<<<std::max(1, sms * 4), 256, 0, stream>>>(L.rings, kNaBuckets, L.ctrl);
     if (pred_mode)
         fill_u64_kernel<<<std::max(1, sms * 8), 256, 0, stream>>>(L.work, cells, ~0ull);
     else
@@ -281,9 +281,6 @@ extern "C" int sssp_solve_noalloc(const int32_t* row_ptr, const uint32_t* arcs, 
         cudaStreamSynchronize(stream) != cudaSuccess)
         return SSSP_E_CUDA;
     if (hc.error == kErrNone && hc.finished) return SSSP_OK;
-    // failure: put the rings back to empty for the next call
-    ring_reset_kernel<<<std::max(1, sms * 4), 256, 0, stream>>>(L.rings, kNaBuckets, L.ctrl);
-    cudaStreamSynchronize(stream);
     if (hc.error == kErrOverflow) return SSSP_E_NOMEM;
     if (hc.error == kErrTimeout) return SSSP_E_TIMEOUT;
     return SSSP_E_CUDA;

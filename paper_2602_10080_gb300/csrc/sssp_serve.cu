@@ -200,7 +200,7 @@ __global__ void serve_reset_kernel(Rings r, uint32_t nrings, Ctrl* ctrl) {
         ctrl->err_where = 0;
         ctrl->err_info = 0;
         ctrl->slice_end = 0;
-        for (int s = 0; s < 32; s++) ctrl->stats[s] = 0;
+        for (int s = 0; s < kStCount; s++) ctrl->stats[s] = 0;
     }
 }
 
@@ -233,6 +233,7 @@ struct Query {
 struct Lane {
     Graph* g = nullptr;
     uint64_t uid = 0;
+    bool counted = false;       // registered in lane_refs (the graph's layout is pinned)
     int pred_mode = 0;
     LaunchPlan plan;
     int vbits = 1;
@@ -332,6 +333,7 @@ void lane_free_buffers(sssp_server* s, Lane* L) {
 
 void lane_destroy(sssp_server* s, Lane* L) {
     lane_free_buffers(s, L);
+    if (L->counted) lane_refs(L->uid, -1);
     if (L->k0) cudaEventDestroy(L->k0);
     if (L->k1) cudaEventDestroy(L->k1);
     if (L->k2) cudaEventDestroy(L->k2);
@@ -507,14 +509,27 @@ Lane* lane_create(sssp_server* s, Graph* g, int pred_mode, int* rc) {
     L->pred_mode = pred_mode;
     sssp_config cfg;
     {
+        // the lane uses the graph's layout as it is now; registering the lane
+        // under the graph's lock keeps a solve from relaying it out meanwhile
         std::lock_guard<std::mutex> lk(g->mu);
-        cfg = g->tuned_valid ? g->tuned : g->defaults;
+        if (const sssp_config* bt = batch_tuned_largest(g)) {
+            // a lane holds many queries at load: the multi-query configuration
+            // of sssp_autotune_batch (its largest size class)
+            cfg = *bt;
+            resolve_auto(g, &cfg);
+        } else {
+            cfg = g->tuned_valid ? g->tuned : g->defaults;
+            resolve_auto(g, &cfg);
+            batch_delta(g, &cfg, 4);   // without one: narrower buckets
+            cfg.bnum = std::min(cfg.bnum, 4);
+        }
+        *rc = validate_config(&cfg);
+        if (!*rc) *rc = plan_launch(g, cfg, pred_mode, true, &L->plan);
+        if (!*rc) {
+            lane_refs(g->uid, 1);
+            L->counted = true;
+        }
     }
-    resolve_auto(g, &cfg);
-    batch_delta(g, &cfg, 4);   // a lane holds many queries at load: narrower buckets
-    cfg.bnum = std::min(cfg.bnum, 4);
-    *rc = validate_config(&cfg);
-    if (!*rc) *rc = plan_launch(g, cfg, pred_mode, true, &L->plan);
     if (*rc) {
         delete L;
         return nullptr;

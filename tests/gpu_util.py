@@ -1,5 +1,8 @@
 """Helpers for the GPU tests: run the C ABI through the Python binding on
 torch CUDA buffers and compare with the oracle."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import torch
 
@@ -10,8 +13,14 @@ U32_INF = 0xFFFFFFFF
 
 
 def cfg(**kw):
+    """The library's default configuration with the given fields set.  A key
+    that is not a field of sssp_config raises (ctypes would accept any
+    attribute name silently)."""
     c = S.sssp_config_default()
+    fields = {name for name, _ in S.sssp_config._fields_} - {"reserved"}
     for k, v in kw.items():
+        if k not in fields:
+            raise KeyError(f"sssp_config has no field {k!r}")
         setattr(c, k, v)
     return c
 
@@ -83,3 +92,21 @@ def assert_exact(g, src, dist_bits, pred=None, canonical=None):
     dist_view = dist_bits if g.wtype == "u32" else dist_bits.view(np.float32)
     status, v = oracle.check(g.row_ptr, g.col, g.w, int(src), dist_view, pred, g.wtype)
     assert status == "ok", (status, v)
+
+
+def oracle_threads() -> int:
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def assert_exact_many(g, srcs, dists, preds=None):
+    """assert_exact for every query (row q of dists/preds from srcs[q]), with
+    the oracle runs spread over the host cores."""
+    srcs = [int(s) for s in srcs]
+
+    def one(q):
+        assert_exact(g, srcs[q], dists[q], None if preds is None else preds[q])
+        return q
+
+    with ThreadPoolExecutor(max_workers=oracle_threads()) as ex:
+        done = list(ex.map(one, range(len(srcs))))
+    assert done == list(range(len(srcs)))

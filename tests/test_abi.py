@@ -52,8 +52,8 @@ def test_struct_layouts_match_c(tmp_path):
 int main(void) {{
   printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(sssp_config), sizeof(sssp_features), sizeof(sssp_stats),
          offsetof(sssp_config, timeout_ms), offsetof(sssp_stats, attempts), offsetof(sssp_features, has_zero_w));
-  printf("%zu %zu %zu\\n", offsetof(sssp_config, shards), offsetof(sssp_stats, cycles),
-         offsetof(sssp_config, l2_only));
+  printf("%zu %zu %zu %zu\\n", offsetof(sssp_config, shards), offsetof(sssp_stats, cycles),
+         offsetof(sssp_config, l2_only), offsetof(sssp_stats, window_advances));
   return 0;
 }}
 ''')
@@ -65,7 +65,7 @@ int main(void) {{
                     ctypes.sizeof(sssp.sssp_stats), sssp.sssp_config.timeout_ms.offset,
                     sssp.sssp_stats.attempts.offset, sssp.sssp_features.has_zero_w.offset,
                     sssp.sssp_config.shards.offset, sssp.sssp_stats.cycles.offset,
-                    sssp.sssp_config.l2_only.offset]
+                    sssp.sssp_config.l2_only.offset, sssp.sssp_stats.window_advances.offset]
 
 
 def test_host_only_calls(lib):

@@ -14,7 +14,7 @@ import graphgen as gg
 import oracle
 import paper_2602_10080_gb300 as S
 from golden_io import all_cases
-from gpu_util import assert_exact, cfg, gpu_batch, gpu_solve, oracle_dist, upload
+from gpu_util import assert_exact, assert_exact_many, cfg, gpu_batch, gpu_solve, oracle_dist, upload
 
 pytestmark = pytest.mark.gpu
 
@@ -59,28 +59,65 @@ def test_grid256_all_queue_configs(l1, l2):
     np.testing.assert_array_equal(d2, d)
 
 
+def with_hubs(g, hubs, seed):
+    """g plus `hubs` extra out-arcs from a few vertices (targets and weights
+    from seeded streams, weights within g's range), rows kept in order."""
+    if g.n < 2 or hubs == 0:
+        return g
+    u = gg.uniform_stream(seed, 60, hubs)
+    t = gg.uniform_stream(seed, 61, hubs)
+    x = gg.uniform_stream(seed, 62, hubs)
+    heads = np.array([(seed * 7919 + 104729 * i) % g.n for i in range(3)], np.int64)
+    src = heads[np.minimum((u * 3).astype(np.int64), 2)]
+    dst = np.minimum((t * g.n).astype(np.int64), g.n - 1)
+    if g.wtype == "f32":
+        lo, hi = (float(g.w.min()), float(g.w.max())) if g.m else (0.0, 1.0)
+        wx = (lo + x * (hi - lo)).astype(np.float32)
+    else:
+        lo, hi = (int(g.w.min()), int(g.w.max())) if g.m else (1, 100)
+        wx = (lo + np.minimum((x * (hi - lo + 1)).astype(np.int64), hi - lo)).astype(np.uint32)
+    u0 = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
+    uu = np.concatenate([u0, src])
+    order = np.argsort(uu, kind="stable")
+    col = np.concatenate([g.col.astype(np.int64), dst])[order].astype(np.int32)
+    w = np.concatenate([g.w, wx])[order]
+    row_ptr = np.concatenate([[0], np.cumsum(np.bincount(uu, minlength=g.n))]).astype(np.int32)
+    return gg.Graph(g.name + "+hubs", g.n, len(col), row_ptr, col, w, g.wtype)
+
+
 @pytest.mark.parametrize("seed", range(24))
 def test_random_graphs_stress(seed):
-    """Tiny queue capacities force constant spill/refill; tiny heavy thresholds force tasks."""
+    """Tiny queue capacities force constant spill/refill; a 32-arc hub split
+    threshold turns every vertex above 32 arcs (the planted hubs) into
+    shadow vertices, with and without their own hub rings."""
     rng = np.random.default_rng(seed)
     n = int(rng.integers(1, 3000))
     m = int(rng.integers(0, 12 * n))
     wt = "f32" if seed % 3 == 2 else "u32"
     lo = 0 if seed % 4 == 1 else 1
     g = gg.random_directed(n, m, lo=lo, hi=int(rng.integers(1, 1000)), seed=seed, wtype=wt)
+    g = with_hubs(g, 0 if seed % 6 == 5 else int(rng.integers(100, 1500)), seed)
     G = upload(g)
     c = cfg(l1_type=L1_ALL[seed % 4], l2_type=seed % 2, l1_cap=256, bmax=int(rng.choice([1, 2, 8, 32])),
-            bnum=int(rng.choice([1, 2, 4])), th_heavy=32, split=32, wb=int(rng.choice([0, 1, 4])),
-            block_threads=int(rng.choice([256, 512, 1024])))
+            bnum=int(rng.choice([1, 2, 4])), split_arcs=32, hub_bnum=int(rng.choice([0, 1, 2])),
+            dedup=int(seed % 2), wb=int(rng.choice([0, 1, 4])), block_threads=int(rng.choice([256, 512, 1024])))
     if wt == "u32":
         c.delta_u32 = int(rng.integers(1, 200))
     else:
         c.delta_f32 = float(rng.uniform(0.01, 2.0))
+    max_deg = int(np.diff(g.row_ptr).max()) if g.n else 0
     for src in rng.integers(0, n, size=2):
         d, p = gpu_solve(G, src, pred=True, config=c)
         assert_exact(g, src, d, p)
+        # the layout is rebuilt for the 32-arc threshold at the first solve
+        shadows = G.features()["shadows"]
+        assert (shadows > 0) == (max_deg > 32), (shadows, max_deg)
         d2, _ = gpu_solve(G, src, pred=False, config=c)
         np.testing.assert_array_equal(d2, d)
+    # back to the default threshold: the layout is rebuilt again, same results
+    d3, p3 = gpu_solve(G, int(src), pred=True)
+    assert_exact(g, int(src), d3, p3)
+    assert (G.features()["shadows"] > 0) == (max_deg > 1024)
 
 
 def test_rmat_f32_exact_and_close_to_f64():
@@ -114,6 +151,10 @@ def test_heavy_vertex_shadows():
             assert_exact(g, src, d, p)
             d2, _ = gpu_solve(G, src, pred=False, config=cfg(max_arcs=ma, near_deltas=0.0))
             np.testing.assert_array_equal(d2, d)
+        # hub slices in their own rings, read only near the front
+        for hb in (1, 2):
+            d3, p3 = gpu_solve(G, src, pred=True, config=cfg(hub_bnum=hb))
+            assert_exact(g, src, d3, p3)
     # batch on the split layout (query slices are padded with shadow vertices)
     db, pb = gpu_batch(G, np.array([0, 777, 5, 0], np.int32), pred=True)
     for q, s in enumerate([0, 777, 5, 0]):
@@ -212,6 +253,25 @@ def test_autotune_prior_and_search():
     assert_exact(g, s, d, p)
     d, p = gpu_solve(G, s, pred=True, config=tuned)
     assert_exact(g, s, d, p)
+
+
+def test_autotune_batch_exact():
+    """A multi-query configuration tuned on whole batch launches is cached on
+    the graph for its size class; a later batch with cfg=None uses it and
+    stays exact, with and without predecessors."""
+    g = gg.rmat(14, 16, seed=12)
+    G = upload(g)
+    srcs, _ = gg.giant_sources(g, 64, seed=2)
+    st = torch.from_numpy(srcs.astype(np.int32)).cuda()
+    tuned = G.autotune_batch(st, 1500)
+    heuristic = S.sssp_autotune_batch(G.handle, srcs.astype(np.int32), 0)   # untimed starting point
+    assert tuned.delta_u32 >= 1 and heuristic.delta_u32 >= 1
+    tuned = G.autotune_batch(st, 1500)
+    d, p = gpu_batch(G, srcs, pred=True)
+    assert_exact_many(g, srcs, d, p)
+    d2, _ = gpu_batch(G, srcs, pred=False, config=tuned)
+    np.testing.assert_array_equal(d2, d)
+    G.close()
 
 
 @pytest.mark.parametrize("l2", [S.L2_BUCKET, S.L2_VECTOR])
