@@ -137,6 +137,11 @@ typedef struct sssp_config {
                               once its distance is near the front (0 = they share the rings) */
     int32_t dedup;         /* 1: a warp round writes each improved target once, with the smallest
                               distance (in-warp duplicates, matched with __match_any_sync) */
+    int32_t pending_marks; /* 1: one pending mark per vertex (4 bytes per distance slot): an
+                              improved vertex already queued at an earlier-or-equal bucket is not
+                              queued again, a read takes the mark and relaxes from the current
+                              distance, and a read that finds the mark taken is stale.  Results
+                              are the same; queue traffic drops (0 = queue every improvement) */
     int32_t reserved;      /* must be zero */
 } sssp_config;
 
@@ -181,9 +186,13 @@ typedef struct sssp_stats {
     int64_t window_pull_backs;    /* L2 writes below the bucket window (window moved back) */
     int64_t window_advances;      /* window moves forward past empty buckets */
     int64_t lock_spins;           /* spins on the block locks (L1 near-far / SLF, block staging) */
-    int64_t cycles_fine[3];       /* SM cycles in relaxation rounds (loads + atomics), in their
-                                     pushes, and in batch set-up; zero unless the library is built
-                                     with SSSP_FINE_CYCLES=1 */
+    int64_t cycles_fine[8];       /* SM cycles in relaxation rounds (loads + atomics), in their
+                                     pushes, in batch set-up, in far-staging flushes, in block-lock
+                                     waits, in L2 claims, in reading claimed chunks and in staging
+                                     flushes before a refill; zero unless the library is built with
+                                     SSSP_FINE_CYCLES=1 */
+    int64_t not_queued;           /* improvements not queued because the vertex was pending
+                                     (sssp_config.pending_marks) */
 } sssp_stats;
 
 typedef struct sssp_graph sssp_graph;

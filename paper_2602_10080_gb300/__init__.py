@@ -48,7 +48,8 @@ class sssp_config(ctypes.Structure):
         ("claim", ctypes.c_int32), ("shards", ctypes.c_int32), ("refillers", ctypes.c_int32),
         ("stage", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
         ("timeout_ms", ctypes.c_int32), ("l2_only", ctypes.c_int32), ("split_arcs", ctypes.c_int32),
-        ("hub_bnum", ctypes.c_int32), ("dedup", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("hub_bnum", ctypes.c_int32), ("dedup", ctypes.c_int32), ("pending_marks", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -103,13 +104,14 @@ class sssp_stats(ctypes.Structure):
         ("dup_targets", ctypes.c_int64), ("rounds", ctypes.c_int64), ("refill_tries", ctypes.c_int64),
         ("wait_spins", ctypes.c_int64), ("idle_iters", ctypes.c_int64), ("window_pull_backs", ctypes.c_int64),
         ("window_advances", ctypes.c_int64), ("lock_spins", ctypes.c_int64),
-        ("cycles_fine", ctypes.c_int64 * 3),
+        ("cycles_fine", ctypes.c_int64 * 8), ("not_queued", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("cycles", "pad0", "cycles_fine")}
         d["cycles"] = dict(zip(self.CYCLE_NAMES, list(self.cycles)))
-        d["cycles_fine"] = dict(zip(("rounds", "push", "batch"), list(self.cycles_fine)))
+        d["cycles_fine"] = dict(zip(("rounds", "push", "batch", "far_flush", "lock", "claim", "chunks", "stage"),
+                                    list(self.cycles_fine)))
         return d
 
 

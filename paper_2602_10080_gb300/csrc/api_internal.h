@@ -31,6 +31,8 @@ struct Workspace {
     size_t out_p_n = 0;
     int32_t* srcs = nullptr;
     size_t srcs_n = 0;
+    uint32_t* pend = nullptr;     // pending marks, one per distance slot
+    size_t pend_n = 0;
     unsigned long long* tl = nullptr;   // run-time sampling buffer
     size_t tl_n = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;

@@ -92,6 +92,12 @@ enum : int {
     kCyRound,         // SSSP_FINE_CYCLES: loads and relaxation of the rounds
     kCyPush,          // SSSP_FINE_CYCLES: push_round (routing to L0 / far staging, their flushes)
     kCyBatch,         // SSSP_FINE_CYCLES: batch set-up (stale filter, row offsets, prefix sum)
+    kStMarked,        // improvements not queued: the vertex was pending at an earlier-or-equal bucket
+    kCyFarFlush,      // SSSP_FINE_CYCLES: far_flush (staging, its L2 writes and lock waits)
+    kCyLock,          // SSSP_FINE_CYCLES: waiting for block locks
+    kCyClaim,         // SSSP_FINE_CYCLES: l2_claim (window, probes, read-ticket CAS)
+    kCyChunks,        // SSSP_FINE_CYCLES: waiting for and reading claimed chunks (incl. L1 writes)
+    kCyStage,         // SSSP_FINE_CYCLES: stage_flush
     kStCount
 };
 
@@ -156,6 +162,8 @@ struct KParams {
                              // of each bucket's shards) and are read only from the first hub_bnum
                              // non-empty buckets; 0: they share the rings
     int32_t dedup;           // 1: one write per improved target of a warp round
+    uint32_t* pend;          // pending marks (or null): per distance slot, the lowest bucket at which
+                             // the vertex has a queued element, kInfU32 = none (see relax_batch)
     int32_t scratch_off, far_off, stat_off, stage_off, l1_off;  // byte offsets in dynamic shared memory
     unsigned long long timeout_ns;
     unsigned long long slice_ns;   // serving: end the launch after this long, draining local queues to L2 (0 = run to completion)
@@ -220,6 +228,29 @@ __device__ __forceinline__ uint2 vld(const volatile uint2* p) {
     return make_uint2((uint32_t)x, (uint32_t)(x >> 32));
 }
 
+// A slot of a lock-free shared-memory ring (L1, block staging) as a
+// one-element mailbox: kEmptySlot (key kEmptyKey, distance 0) or an
+// element.  A writer deposits with a 64-bit CAS from empty and a taker
+// withdraws with a 64-bit exchange to empty, so two writers of consecutive
+// laps of the ring cannot both fill one slot, nor two takers both empty it
+// (with plain stores, "empty" cannot tell "cleared by the previous lap's
+// taker" from "not yet filled by the previous lap's writer").
+constexpr unsigned long long kEmptySlot = 0x00000000ffffffffull;
+__device__ __forceinline__ bool slot_try_put(volatile uint2* p, uint2 e) {
+    if (vld(p).x != kEmptyKey) return false;
+    const unsigned long long v = ((unsigned long long)e.y << 32) | e.x;
+    return atomicCAS(const_cast<unsigned long long*>(reinterpret_cast<volatile unsigned long long*>(p)), kEmptySlot,
+                     v) == kEmptySlot;
+}
+__device__ __forceinline__ bool slot_try_take(volatile uint2* p, uint2& e) {
+    if (vld(p).x == kEmptyKey) return false;
+    const unsigned long long y =
+        atomicExch(const_cast<unsigned long long*>(reinterpret_cast<volatile unsigned long long*>(p)), kEmptySlot);
+    if (y == kEmptySlot) return false;
+    e = make_uint2((uint32_t)y, (uint32_t)(y >> 32));
+    return true;
+}
+
 // Ticket w is ahead of ticket r (wrap-safe): some writer holds ticket r.
 // Any observed w with w - r > 0 proves ticket r was taken, whatever the order
 // in which the two relaxed loads were performed.
@@ -236,6 +267,12 @@ __device__ __forceinline__ bool ahead(uint32_t w, uint32_t r) { return (int32_t)
 #endif
 #ifndef SSSP_FINE_CYCLES
 #define SSSP_FINE_CYCLES 0
+#endif
+#ifndef SSSP_BULK_REFILL
+#define SSSP_BULK_REFILL 1
+#endif
+#ifndef SSSP_LF_STAGE
+#define SSSP_LF_STAGE 1
 #endif
 #ifndef SSSP_SPEC_ROW
 #define SSSP_SPEC_ROW 0
@@ -293,6 +330,20 @@ __device__ __forceinline__ unsigned long long ld_dist(const unsigned long long* 
     return __ldcg(p);
 #endif
 }
+// Pending-mark atomics: an improvement lowers the mark with release order
+// (its distance write is visible to whoever takes the mark later); a read
+// takes the mark with acquire order and only then loads the distance.
+__device__ __forceinline__ uint32_t atom_min_release(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.release.gpu.global.min.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ uint32_t atom_exch_acquire(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acquire.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // distance minimum whose old value is not needed (a reduction)
 __device__ __forceinline__ void red_min(uint32_t* p, uint32_t v) {
 #if SSSP_L2_HINTS
@@ -363,7 +414,9 @@ struct BlockShared {
     uint32_t nf;                  // NF threshold (distance bits)
     uint32_t writes;              // L1 write calls (periodic flush)
     unsigned long long acct;      // (held elements << 32) | unpublished L2 reads
-    uint32_t scnt[32];            // elements staged per L2 bucket ring index
+    uint32_t scnt[32];            // staging per L2 bucket ring index: elements staged (lock-free
+                                  // staging: the ring's tail)
+    uint32_t shead[32];           // lock-free staging: the ring's head (slots taken for L2)
     unsigned long long slice_end; // serving: end of this launch's slice (globaltimer), ~0 = none
     unsigned long long deadline;  // watchdog: globaltimer value after which waits give up
     unsigned long long t0;        // launch start (globaltimer), for run-time sampling
@@ -534,6 +587,9 @@ struct Worker {
     __device__ bool lock(int* word) {
         int ok = 1;
         mark(2);
+#if SSSP_FINE_CYCLES
+        const long long cl0 = clock64();
+#endif
         if (lane == 0) {
             uint32_t spins = 0, ns = 16;
             for (;;) {
@@ -547,6 +603,9 @@ struct Worker {
                 ns = ns < 256u ? ns * 2u : 256u;
             }
             sst()[kStLockSpin] += spins;
+#if SSSP_FINE_CYCLES
+            sst()[kCyLock] += (unsigned long long)(clock64() - cl0);
+#endif
         }
         ok = __shfl_sync(kFull, ok, 0);
         __threadfence_block();
@@ -940,13 +999,13 @@ struct Worker {
     }
 
     // ---- L1 vector / filter policies: lock-free ring ------------------------
-    // Slots hold an element or kEmptyKey (64-bit stores, so a slot is seen
-    // whole).  Writers reserve slots by CAS on tail (bounded by head + cap),
-    // wait for each reserved slot to be empty (its reader of the previous
-    // lap has cleared it) and store; readers reserve up to 32 slots by CAS on
-    // head (bounded by tail), wait for each slot to be filled, take it and
-    // clear it.  Both waits are on warps that are already inside the same
-    // operation, so they are short; they are bounded by the deadline.
+    // Slots are one-element mailboxes (slot_try_put / slot_try_take).
+    // Writers reserve slots by CAS on tail (bounded by head + cap) and deposit
+    // into each reserved slot once it is empty (its reader of the previous
+    // lap has taken the element); readers reserve up to 32 slots by CAS on
+    // head (bounded by tail) and withdraw from each once it is full.  Both
+    // waits are on warps that are already inside the same operation, so they
+    // are short; they are bounded by the deadline.
     __device__ __forceinline__ bool l1_lockfree() const { return P.l1_type == 0 || P.l1_type == 2; }
 
     template <int K>
@@ -988,14 +1047,13 @@ struct Worker {
             if (placed) {
                 volatile uint2* slot = &L1()[(base + rank) & l1_mask()];
                 uint32_t spins = 0;
-                while (vld(slot).x != kEmptyKey) {
+                while (!slot_try_put(slot, e[k])) {
                     if ((++spins & 255u) == 0 && expired()) {
                         raise_error(P.ctrl, kErrTimeout, 10, 0);
                         ok = 0;
                         break;
                     }
                 }
-                if (ok) vst(slot, e[k]);
             }
             __syncwarp();
         }
@@ -1023,17 +1081,15 @@ struct Worker {
         if (lane < c) {
             volatile uint2* slot = &L1()[(h + lane) & l1_mask()];
             uint32_t spins = 0;
-            uint2 x = vld(slot);
-            while (x.x == kEmptyKey) {
+            uint2 x = make_uint2(kEmptyKey, 0u);
+            while (!slot_try_take(slot, x)) {
                 if ((++spins & 255u) == 0 && expired()) {
                     raise_error(P.ctrl, kErrTimeout, 11, 0);
                     break;
                 }
-                x = vld(slot);
             }
             valid = x.x != kEmptyKey;
             e = x;
-            vst(slot, make_uint2(kEmptyKey, 0u));
         }
         __syncwarp();
         stat(kStPopL1, 1);
@@ -1167,6 +1223,90 @@ struct Worker {
         return __shfl_sync(kFull, f, 0);
     }
 
+    // The claimed chunks t .. t + got - 1 of `ring` (counts: chunk j's in lane
+    // j) read together: chunk 0 becomes this warp's batch, chunks 1 .. got - 1
+    // go to the lock-free L1 in one reservation.  The chunk loads are issued
+    // in groups of four, then every chunk slot is released at once (lane j
+    // releases chunk j).  Returns false, having read nothing, when L1 has no
+    // room for all of them (the caller reads chunk by chunk instead).
+    __device__ bool read_chunks_bulk(uint32_t ring, uint32_t t, uint32_t got, uint32_t cnt, bool& valid, uint2& e) {
+        // exclusive prefix of the counts of chunks 1 .. got - 1 (lane j)
+        const uint32_t mine = (lane >= 1u && lane < got) ? cnt : 0u;
+        uint32_t incl = mine;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(kFull, incl, o);
+            if (lane >= (uint32_t)o) incl += x;
+        }
+        const uint32_t rest = __shfl_sync(kFull, incl, kMaxClaim - 1);
+        const uint32_t pre = incl - mine;
+        // all-or-nothing reservation of `rest` L1 slots
+        uint32_t base = 0;
+        int ok = 1;
+        if (lane == 0 && rest) {
+            const uint32_t cap = (uint32_t)P.l1_cap;
+            uint32_t tl = *(volatile uint32_t*)&S()->tail;
+            for (;;) {
+                const uint32_t h = *(volatile uint32_t*)&S()->head;
+                if (tl - h + rest > cap) {
+                    ok = 0;
+                    break;
+                }
+                const uint32_t old = atomicCAS(&S()->tail, tl, tl + rest);
+                if (old == tl) break;
+                tl = old;
+            }
+            base = tl;
+        }
+        if (!__shfl_sync(kFull, ok, 0)) return false;
+        base = __shfl_sync(kFull, base, 0);
+        const size_t slot0 = (size_t)ring * P.l2.nch;
+        const uint32_t mask = P.l2.nch - 1u;
+        // chunk 0: this warp's batch
+        {
+            const uint32_t c0 = __shfl_sync(kFull, cnt, 0);
+            valid = lane < c0;
+            if (valid) e = P.l2.data[(slot0 + (t & mask)) * kChunk + lane];
+            count_live(valid, e.x, -1);
+        }
+        // chunks 1 .. got - 1 into L1, four loads in flight per lane
+#pragma unroll
+        for (uint32_t j0 = 1; j0 < (uint32_t)kMaxClaim; j0 += 4) {
+            uint2 x[4];
+            bool v[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; k++) {
+                const uint32_t j = j0 + k;
+                const uint32_t cj = __shfl_sync(kFull, cnt, j & 31u);
+                v[k] = j < got && lane < cj;
+                x[k] = v[k] ? P.l2.data[(slot0 + ((t + j) & mask)) * kChunk + lane] : make_uint2(0u, 0u);
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; k++) {
+                const uint32_t j = j0 + k;
+                const uint32_t pj = __shfl_sync(kFull, pre, j & 31u);
+                count_live(v[k], x[k].x, -1);
+                if (v[k]) {
+                    volatile uint2* sl = &L1()[(base + pj + lane) & l1_mask()];
+                    uint32_t spins = 0;
+                    while (!slot_try_put(sl, x[k])) {
+                        if ((++spins & 255u) == 0 && expired()) {
+                            raise_error(P.ctrl, kErrTimeout, 12, 0);
+                            break;
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < got) {
+            fence_gpu();
+            st_release(P.l2.seq + slot0 + ((t + lane) & mask), t + lane + P.l2.nch);
+        }
+        __syncwarp();
+        return true;
+    }
+
     // L1 is empty: up to `refillers` warps of the block at a time refill it
     // from L2 (Section 3.2: an empty level triggers a read of the next level).
     // The first claimed chunk becomes this warp's batch, the rest go to L1.
@@ -1182,12 +1322,25 @@ struct Worker {
         role = __shfl_sync(kFull, role, 0);
         if (!role) return -1;
         stat(kStRefillTry, 1);
+#if SSSP_FINE_CYCLES
+        const long long cs0 = clock64();
         stage_flush(false);
+        stat(kCyStage, (unsigned long long)(clock64() - cs0));
+#else
+        stage_flush(false);
+#endif
         uint32_t want = (uint32_t)P.claim;
         const uint32_t room = l1_free() / kChunk;
         if (want > room + 1u) want = room + 1u;
         uint32_t ring = 0, t = 0;
+#if SSSP_FINE_CYCLES
+        const long long cc0 = clock64();
+#endif
         const uint32_t got = l2_claim(want, ring, t);
+#if SSSP_FINE_CYCLES
+        const long long cc1 = clock64();
+        stat(kCyClaim, (unsigned long long)(cc1 - cc0));
+#endif
         int result = 0;
         if (got) {
             bool okr = true;
@@ -1199,18 +1352,23 @@ struct Worker {
                 if (lane == 0)
                     atomicAdd(&S()->acct, ((unsigned long long)total << 32) | (unsigned long long)total);
                 const uint32_t c0 = __shfl_sync(kFull, cnt, 0);
-                l2_read_chunk(ring, t, c0, valid, e);
-                for (uint32_t j = 1; j < got; j++) {
-                    const uint32_t cj = __shfl_sync(kFull, cnt, j);
-                    bool v2 = false;
-                    uint2 x[1] = {make_uint2(0, 0)};
-                    l2_read_chunk(ring, t + j, cj, v2, x[0]);
-                    bool vv[1] = {v2};
-                    // chunks taken from L2 for processing bypass the L1 filter
-                    l1_write<1>(x, vv, 0, false);
+                if (!(SSSP_BULK_REFILL && got > 1 && l1_lockfree() && read_chunks_bulk(ring, t, got, cnt, valid, e))) {
+                    l2_read_chunk(ring, t, c0, valid, e);
+                    for (uint32_t j = 1; j < got; j++) {
+                        const uint32_t cj = __shfl_sync(kFull, cnt, j);
+                        bool v2 = false;
+                        uint2 x[1] = {make_uint2(0, 0)};
+                        l2_read_chunk(ring, t + j, cj, v2, x[0]);
+                        bool vv[1] = {v2};
+                        // chunks taken from L2 for processing bypass the L1 filter
+                        l1_write<1>(x, vv, 0, false);
+                    }
                 }
                 stat(kStPopL2, (unsigned long long)got);
                 stat(kStRefill, 1);
+#if SSSP_FINE_CYCLES
+                stat(kCyChunks, (unsigned long long)(clock64() - cc1));
+#endif
                 result = c0 ? 1 : (total ? 2 : 0);
             }
         }
@@ -1324,6 +1482,124 @@ struct Worker {
         return ab % (uint32_t)P.bmax;
     }
 
+    // ---- lock-free block staging (SSSP_LF_STAGE) ----------------------------
+    // One ring of kStageCap slots per L2 bucket ring index b, tail scnt[b] and
+    // head shead[b], with mailbox slots as in the lock-free L1.  Writers
+    // reserve slots with a CAS on the tail bounded by head + kStageCap and
+    // deposit; a taker reserves up to 32 slots with a CAS on the head and
+    // withdraws.  No block lock.
+    __device__ __forceinline__ volatile uint2* stg_slot(uint32_t b, uint32_t i) const {
+        return reinterpret_cast<volatile uint2*>(stg()) + b * (uint32_t)kStageCap + (i & (uint32_t)(kStageCap - 1));
+    }
+
+    // Reads the reserved slots h .. h + c - 1 of bucket b into the lanes and clears them.
+    __device__ void stage_read(uint32_t b, uint32_t h, uint32_t c, bool& v, uint2& x) {
+        v = lane < c;
+        if (v) {
+            volatile uint2* sl = stg_slot(b, h + lane);
+            uint2 y = make_uint2(kEmptyKey, 0u);
+            uint32_t spins = 0;
+            while (!slot_try_take(sl, y)) {
+                if ((++spins & 255u) == 0 && expired()) {
+                    raise_error(P.ctrl, kErrTimeout, 13, (int)b);
+                    break;
+                }
+            }
+            v = y.x != kEmptyKey;
+            x = y;
+        }
+        __syncwarp();
+    }
+
+    // Takes up to 32 staged elements of bucket b (lock-free); returns the count.
+    __device__ uint32_t stage_take_lf(uint32_t b, bool& v, uint2& x) {
+        uint32_t h = 0, c = 0;
+        if (lane == 0) {
+            h = *(volatile uint32_t*)&S()->shead[b];
+            for (;;) {
+                const uint32_t t = *(volatile uint32_t*)&S()->scnt[b];
+                c = t - h < 32u ? t - h : 32u;
+                if (c == 0) break;
+                const uint32_t old = atomicCAS(&S()->shead[b], h, h + c);
+                if (old == h) break;
+                h = old;
+            }
+        }
+        c = __shfl_sync(kFull, c, 0);
+        h = __shfl_sync(kFull, h, 0);
+        v = false;
+        if (c) stage_read(b, h, c, v, x);
+        return c;
+    }
+
+    // Places the lanes' staged elements sv (bucket b each) in their buckets'
+    // rings; elements that do not fit go to L2 at once.  A bucket that now
+    // holds a full chunk is shipped to L2.  One bucket ring at a time: every
+    // reservation is filled, and every chunk taken is read and cleared,
+    // before the warp touches another ring.  Within one ring no wait can
+    // close a cycle (a taker waits only for slots at most 31 ahead of what
+    // it holds, a writer only for slots at least 33 behind what it reserved,
+    // with kStageCap = 64 and at most 32 per reservation); a warp waiting in
+    // one ring while holding slots of another could (the lanes re-converge
+    // after each wait loop).
+    __device__ void stage_place_lf(bool sv, uint2 x, uint32_t b) {
+        bool over = false;
+        uint32_t todo = __ballot_sync(kFull, sv);
+        while (todo) {
+            const uint32_t bg = __shfl_sync(kFull, b, __ffs(todo) - 1);
+            const bool in = sv && b == bg;
+            const uint32_t grp = __ballot_sync(kFull, in);
+            todo &= ~grp;
+            uint32_t base = 0, take = 0;
+            if (lane == 0) {
+                const uint32_t k = (uint32_t)__popc(grp);
+                uint32_t t = *(volatile uint32_t*)&S()->scnt[bg];
+                for (;;) {
+                    const uint32_t h = *(volatile uint32_t*)&S()->shead[bg];
+                    const uint32_t used = t - h;
+                    take = used < (uint32_t)kStageCap ? min(k, (uint32_t)kStageCap - used) : 0u;
+                    if (take == 0) break;
+                    const uint32_t old = atomicCAS(&S()->scnt[bg], t, t + take);
+                    if (old == t) break;
+                    t = old;
+                }
+                base = t;
+            }
+            base = __shfl_sync(kFull, base, 0);
+            take = __shfl_sync(kFull, take, 0);
+            const uint32_t rank = __popc(grp & lanemask_lt());
+            const bool placed = in && rank < take;
+            over = over || (in && !placed);
+            if (placed) {
+                volatile uint2* sl = stg_slot(bg, base + rank);
+                uint32_t spins = 0;
+                while (!slot_try_put(sl, x)) {
+                    if ((++spins & 255u) == 0 && expired()) {
+                        raise_error(P.ctrl, kErrTimeout, 14, (int)bg);
+                        break;
+                    }
+                }
+            }
+            __syncwarp();
+            // a full chunk of this bucket goes to L2
+            uint32_t h = 0;
+            int own = 0;
+            if (lane == 0) {
+                h = *(volatile uint32_t*)&S()->shead[bg];
+                const uint32_t t = *(volatile uint32_t*)&S()->scnt[bg];
+                own = t - h >= 32u && atomicCAS(&S()->shead[bg], h, h + 32u) == h;
+            }
+            if (__shfl_sync(kFull, own, 0)) {
+                h = __shfl_sync(kFull, h, 0);
+                bool vy = false;
+                uint2 y = make_uint2(0, 0);
+                stage_read(bg, h, 32u, vy, y);
+                dec += l2_write(vy, y);
+            }
+        }
+        dec += l2_write(over, x);
+    }
+
     // Takes up to 32 staged elements of bucket ring index b (lock held).
     __device__ uint32_t stage_take(uint32_t b, bool& v, uint2& x) {
         const uint32_t c0 = sread(&S()->scnt[b]);
@@ -1349,15 +1625,22 @@ struct Worker {
             const uint32_t b = lane;
             const bool cand = b < (uint32_t)P.bmax &&
                               (all || b == W % (uint32_t)P.bmax || b == (W + 1u) % (uint32_t)P.bmax);
-            if (cand) cnt = *(volatile uint32_t*)&S()->scnt[b];
+            if (cand) {
+                cnt = *(volatile uint32_t*)&S()->scnt[b];
+                if (SSSP_LF_STAGE) cnt -= *(volatile uint32_t*)&S()->shead[b];
+            }
             const uint32_t m = __ballot_sync(kFull, cand && cnt > 0u);
             if (!m) return;
             const uint32_t bf = (uint32_t)(__ffs(m) - 1);
             bool v = false;
             uint2 x = make_uint2(0, 0);
+#if SSSP_LF_STAGE
+            stage_take_lf(bf, v, x);
+#else
             if (!slock()) return;
             stage_take(bf, v, x);
             sunlock();
+#endif
             dec += l2_write(v, x);
         }
     }
@@ -1384,6 +1667,15 @@ struct Worker {
             dec += l2_write(urgent, x);
             const bool sv = v && !urgent;
             if (!__any_sync(kFull, sv)) continue;
+#if SSSP_LF_STAGE
+            // the staged elements become visible to the block: count every
+            // private push now (counting early only delays the done flush)
+            if (lane == 0 && unc != 0) atomicAdd(&S()->acct, ((unsigned long long)(uint32_t)unc) << 32);
+            unc = 0;
+            __syncwarp();
+            stage_place_lf(sv, x, b);
+            continue;
+#endif
             bool vy = false, over = false;
             uint2 y = make_uint2(0, 0);
             if (!slock()) return;
@@ -1418,6 +1710,9 @@ struct Worker {
         uint32_t m = __ballot_sync(kFull, f);
         if (!m) return;
         uint32_t c = __popc(m);
+#if SSSP_FINE_CYCLES
+        const long long cf0 = clock64();
+#endif
         if (nfar + c > (uint32_t)kFarCap) far_flush(0);
         if (f) farbuf()[nfar + __popc(m & lanemask_lt())] = x;
         __syncwarp();
@@ -1425,6 +1720,9 @@ struct Worker {
         unc += (int)c;
         stat(kStFar, (unsigned long long)(c));
         if (nfar >= 32u) far_flush(nfar & 31u);
+#if SSSP_FINE_CYCLES
+        stat(kCyFarFlush, (unsigned long long)(clock64() - cf0));
+#endif
     }
 
     // ---- relaxation ---------------------------------------------------------
@@ -1499,8 +1797,23 @@ struct Worker {
     // goes to L2 like a heavy one (delta-stepping relaxes light arcs within
     // the current bucket only).  With admission offsets (serving) front is a
     // bucket, otherwise a distance.
-    __device__ __forceinline__ void push_round(bool imp, uint32_t key, uint32_t nd, uint32_t w, uint32_t front) {
-        stat(kStImproved, (unsigned long long)(__popc(__ballot_sync(kFull, imp))));
+    // n_imp / n_mark: per-batch counts of improvements and of improvements not
+    // queued (pending marks), added to the statistics once per batch
+    __device__ __forceinline__ void push_round(bool imp, uint32_t key, uint32_t nd, uint32_t w, uint32_t front,
+                                               uint32_t& n_imp, uint32_t& n_mark) {
+        n_imp += (uint32_t)__popc(__ballot_sync(kFull, imp));
+        if (P.pend) {
+            // an improved vertex already queued at an earlier-or-equal bucket
+            // is not queued again: its queued element is relaxed with the
+            // distance current when it is read
+            bool q = false;
+            if (imp) {
+                const uint32_t b = abs_bucket(key, nd);
+                q = atom_min_release(P.pend + dist_index(key), b) > b;
+            }
+            n_mark += (uint32_t)__popc(__ballot_sync(kFull, imp && !q));
+            imp = q;
+        }
         if (P.dedup) {
             // in-warp duplicates (Listing 1's write of a warp's improved
             // vertices): lanes whose arcs improved the same target this round
@@ -1580,7 +1893,24 @@ struct Worker {
             raise_error(P.ctrl, kErrElement, 8, (int)key);
             valid = false;
         }
-        if (valid) {
+        if (valid && P.pend) {
+            // pending marks: the read takes the vertex's mark; a mark already
+            // taken by an earlier read means no improvement since that read's
+            // relaxation, so the element is stale.  Otherwise the arcs are
+            // relaxed from the current distance (never above the element's).
+            const uint32_t v = key_vertex(key);
+            const int32_t r0 = ld_row(P.row_ptr + v), r1 = ld_row(P.row_ptr + v + 1);
+            const uint32_t mark = atom_exch_acquire(P.pend + dist_index(key), kInfU32);
+            if (mark == kInfU32) {
+                valid = false;
+                stale = true;
+            } else {
+                du = dpart(ld_dist(dist() + dist_index(key)));
+                el.y = du;
+                rs = r0;
+                deg = r1 - r0;
+            }
+        } else if (valid) {
 #if SSSP_SPEC_ROW
             // the row offsets are loaded alongside the distance (one memory
             // round trip instead of two); a stale vertex ignores them
@@ -1620,6 +1950,8 @@ struct Worker {
         const bool defer = valid && ex >= P.max_arcs;
         const uint32_t dm = __ballot_sync(kFull, defer);
         if (dm) {
+            // a deferred vertex is queued again (in L0): it gets its mark back
+            if (defer && P.pend) atomicMin(P.pend + dist_index(key), abs_bucket(key, el.y));
             if (defer) scratch()[__popc(dm & lanemask_lt())] = el;
             __syncwarp();
             l0_push(__popc(dm), true);
@@ -1663,6 +1995,7 @@ struct Worker {
             const int32_t shs = __reduce_add_sync(kFull, (uint32_t)sh);
             if (shs) stat(kStRelaxShadow, (unsigned long long)shs);
         }
+        uint32_t n_imp = 0, n_mark = 0, n_rounds = 0;
 #if SSSP_PIPELINE
         // the next round's arcs are loaded while this round's distances are
         RoundIn nx = round_in(0, total, ex, rs, du, myq, pu);
@@ -1673,7 +2006,6 @@ struct Worker {
                 if (lane == 0) stop = expired() || ld_volatile_int(&P.ctrl->error) != 0;
                 if (__shfl_sync(kFull, stop, 0)) break;
             }
-            stat(kStRounds, 1);
 #if SSSP_FINE_CYCLES
             const long long cr0 = clock64();
 #endif
@@ -1693,11 +2025,15 @@ struct Worker {
             const long long cr1 = clock64();
             stat(kCyRound, (unsigned long long)__shfl_sync(kFull, (unsigned long long)(cr1 - cr0), 0));
 #endif
-            push_round(imp, MQ ? ((cu.q << P.vbits) | cu.a.x) : cu.a.x, nd, cu.a.y, front);
+            push_round(imp, MQ ? ((cu.q << P.vbits) | cu.a.x) : cu.a.x, nd, cu.a.y, front, n_imp, n_mark);
+            n_rounds++;
 #if SSSP_FINE_CYCLES
             stat(kCyPush, (unsigned long long)(clock64() - cr1));
 #endif
         }
+        stat(kStRounds, n_rounds);
+        stat(kStImproved, n_imp);
+        if (n_mark) stat(kStMarked, n_mark);
         return consumed;
     }
 
@@ -1896,7 +2232,7 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
         S->head = S->tail = S->fhead = S->ftail = 0;
         S->writes = 0;
         S->acct = 0ull;
-        for (int i = 0; i < 32; i++) S->scnt[i] = 0;
+        for (int i = 0; i < 32; i++) S->scnt[i] = S->shead[i] = 0;
         unsigned long long win = ld_acquire64(&P.ctrl->window);
         S->nf = Arith<WT>::upper((uint32_t)win, P.delta, 1.0f);
         S->deadline = gtime() + P.timeout_ns;
@@ -1913,6 +2249,10 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
         }
     }
     for (int i = threadIdx.x; i < P.l1_cap; i += blockDim.x) vst(l1 + i, make_uint2(kEmptyKey, 0u));
+    if (SSSP_LF_STAGE && P.stage) {
+        volatile uint2* st = reinterpret_cast<volatile uint2*>(mlmq_smem + P.stage_off);
+        for (int i = threadIdx.x; i < P.bmax * kStageCap; i += blockDim.x) vst(st + i, make_uint2(kEmptyKey, 0u));
+    }
     __syncthreads();
     Worker<WT, PRED, MQ, R> w(P);
     w.run();

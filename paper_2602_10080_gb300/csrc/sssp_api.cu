@@ -159,6 +159,7 @@ __global__ void seed_kernel(KParams P, const int32_t* srcs, int32_t src0, int32_
             uint32_t key = P.vbits ? (((uint32_t)q << P.vbits) | (uint32_t)s) : (uint32_t)s;
             P.l2.data[slot * kChunk + lane] = make_uint2(key, 0u);
             size_t di = (size_t)q * (size_t)P.nv + (size_t)s;
+            if (P.pend) P.pend[di] = 0u;   // queued at bucket 0
             if (packed)
                 reinterpret_cast<unsigned long long*>(P.dist)[di] = (unsigned long long)(uint32_t)s;
             else
@@ -316,6 +317,7 @@ void Workspace::release() {
     cudaFree(out_d);
     cudaFree(out_p);
     cudaFree(srcs);
+    cudaFree(pend);
     cudaFree(tl);
     if (host_ctrl) cudaFreeHost(host_ctrl);
     if (ev0) cudaEventDestroy(ev0);
@@ -419,6 +421,7 @@ static void config_defaults(sssp_config* c) {
     c->split_arcs = 0;
     c->hub_bnum = 0;
     c->dedup = 0;
+    c->pending_marks = 1;
 }
 
 // Fills auto fields from the graph features (the prior of Section 3.5).
@@ -495,6 +498,7 @@ int validate_config(const sssp_config* c) {
     if (c->l2_only < 0 || c->l2_only > 1) return SSSP_E_INVAL;
     if (c->split_arcs != 0 && (c->split_arcs < 32 || c->split_arcs > (1 << 30))) return SSSP_E_INVAL;
     if (c->hub_bnum < 0 || c->hub_bnum > 32 || c->dedup < 0 || c->dedup > 1) return SSSP_E_INVAL;
+    if (c->pending_marks < 0 || c->pending_marks > 1) return SSSP_E_INVAL;
     if (c->reserved != 0) return SSSP_E_INVAL;
     return SSSP_OK;
 }
@@ -657,9 +661,16 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
             srcs_d = ws.srcs;
         }
 
+        uint32_t* pend = nullptr;
+        if (cfg.pending_marks) {
+            rc = grow(&ws.pend, &ws.pend_n, cells);
+            if (rc) return rc;
+            pend = ws.pend;
+        }
         KParams P = plan.P;
         P.nq = nq;
         P.dist = work;
+        P.pend = pend;
         P.vbits = mq ? vbits : 0;
         P.vmask = mq ? ((1u << vbits) - 1u) : 0xffffffffu;
         P.l2 = ws.rings;
@@ -672,6 +683,7 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
         else
             fill_u32_kernel<<<grid_for(cells, g->sms), 256, 0, stream>>>(
                 (uint32_t*)work, cells, f32 ? kInfF32 : kInfU32);
+        if (pend) fill_u32_kernel<<<grid_for(cells, g->sms), 256, 0, stream>>>(pend, cells, kInfU32);
         seed_kernel<<<1, 32, 0, stream>>>(P, srcs_d, src0, nq, pred_mode ? 1 : 0);
         cudaEventRecord(ws.ev1, stream);
         // run-time sampling (sssp_solve_sampled, or SSSP_DEBUG >= 4: printed)
@@ -817,6 +829,12 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
         st.cycles_fine[0] = (int64_t)hc.stats[kCyRound];
         st.cycles_fine[1] = (int64_t)hc.stats[kCyPush];
         st.cycles_fine[2] = (int64_t)hc.stats[kCyBatch];
+        st.cycles_fine[3] = (int64_t)hc.stats[kCyFarFlush];
+        st.cycles_fine[4] = (int64_t)hc.stats[kCyLock];
+        st.cycles_fine[5] = (int64_t)hc.stats[kCyClaim];
+        st.cycles_fine[6] = (int64_t)hc.stats[kCyChunks];
+        st.cycles_fine[7] = (int64_t)hc.stats[kCyStage];
+        st.not_queued = (int64_t)hc.stats[kStMarked];
         g->last = st;
         if (st_out) *st_out = st;
         if (dbg > 1)

@@ -821,6 +821,9 @@ int collect_lane(sssp_server* s, Lane* L) {
                 hc.error = (s->opt.flags & SSSP_SERVE_INJECT_OVERFLOW) ? kErrOverflow : kErrTimeout;
         }
         if (hc.error != kErrNone) {
+            if (s->debug)
+                std::fprintf(stderr, "[sssp serve] slice error %d at %d (info %d), lane n=%d pred=%d cap=%u\n",
+                             hc.error, hc.err_where, hc.err_info, L->g->n, L->pred_mode, L->cap);
             if (hc.error == kErrOverflow) {
                 int rc = lane_restart(s, L);
                 if (rc == SSSP_E_CUDA) return rc;
