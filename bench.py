@@ -66,7 +66,8 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-TRAFFIC_CONFIG_KEYS = ("l1_type", "l2_type", "delta_u32", "bnum", "bmax", "claim", "block_threads")
+TRAFFIC_CONFIG_KEYS = ("l1_type", "l2_type", "delta_u32", "bnum", "bmax", "claim", "block_threads", "split_arcs",
+                       "hub_bnum", "pending_marks")
 
 
 def config_signature(cfg) -> str:
@@ -262,10 +263,12 @@ def run_reference(args):
     return 0
 
 
-def batch_leg(S, gg, torch, wtype: str = "u32", nq: int = 256, seq_sample: int = 32):
+def batch_leg(S, gg, torch, wtype: str = "u32", nq: int = 256, seq_sample: int = 32, tune_ms: int = 8000):
     """Batched throughput: nq sources of R-MAT 20 in one persistent launch
     (sssp_solve_batch, dist nq x n on the device) against one-at-a-time
-    sssp_solve calls on the same sources (a timed sample of them)."""
+    sssp_solve calls on the same sources (a timed sample of them), first
+    with the library's multi-query heuristic, then with the configuration
+    sssp_autotune_batch picks for this batch size (timed whole launches)."""
     g = gg.workload("rmat20" if wtype == "u32" else "rmat20f")
     srcs, _ = gg.giant_sources(g, nq, seed=2)
     G = S.Graph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda(),
@@ -284,6 +287,15 @@ def batch_leg(S, gg, torch, wtype: str = "u32", nq: int = 256, seq_sample: int =
         e1.record(stream)
         torch.cuda.synchronize()
         batch_s = e0.elapsed_time(e1) / 1e3 / reps
+        tuned = G.autotune_batch(st, tune_ms)          # cached on the graph for this size class
+        G.solve_batch(st, out, None, None, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            G.solve_batch(st, out, None, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tuned_s = e0.elapsed_time(e1) / 1e3 / reps
         one = torch.empty(g.n, dtype=torch.int32, device="cuda")
         for s in srcs[:3]:
             G.solve(int(s), one, None, None, stream)
@@ -299,7 +311,12 @@ def batch_leg(S, gg, torch, wtype: str = "u32", nq: int = 256, seq_sample: int =
                 "dtype": wtype, "qps": round(len(srcs) / batch_s, 1), "ms_per_batch": round(batch_s * 1e3, 2),
                 "sequential_qps": round(1.0 / seq_s, 1),
                 "sequential_sample": f"{k} sssp_solve calls",
-                "speedup": round(seq_s * len(srcs) / batch_s, 2)}
+                "speedup": round(seq_s * len(srcs) / batch_s, 2),
+                "tuned": {"qps": round(len(srcs) / tuned_s, 1), "ms_per_batch": round(tuned_s * 1e3, 2),
+                          "speedup": round(seq_s * len(srcs) / tuned_s, 2), "budget_ms": tune_ms,
+                          "config": {k2: v for k2, v in tuned.as_dict().items()
+                                     if k2 in ("delta_u32", "delta_f32", "bnum", "l1_cap", "claim", "refillers",
+                                               "hub_bnum")}}}
     finally:
         G.close()
 
@@ -606,7 +623,8 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": round(e2e_value, 3), "unit": "GTEPS", "h2d_bytes_per_step": 4,
                 "d2h_bytes_per_step": 8 * g.n},
-        "gpu_launches": 4 * args.steps,
+        # per solve: distance fill, [pending-mark fill], seed, relaxation, unpack
+        "gpu_launches": (4 + int(tuned.pending_marks)) * args.steps,
         "roofline": roof,
         "clocks": clk.summary(),
         "per_source": {"kernel_ms": percentiles(kernel_ms),

@@ -56,9 +56,15 @@ namespace sssp {
 constexpr int kWarp = 32;
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kChunk = 32;          // elements per L2 chunk
-constexpr int kFarCap = 64;         // per-warp far staging (elements)
+#ifndef SSSP_FAR_CAP
+#define SSSP_FAR_CAP 64
+#endif
+#ifndef SSSP_STAGE_CAP
+#define SSSP_STAGE_CAP 64
+#endif
+constexpr int kFarCap = SSSP_FAR_CAP;  // per-warp far staging (elements)
 constexpr int kMaxClaim = 8;        // chunks per L2 claim (upper bound)
-constexpr int kStageCap = 64;       // block staging per L2 bucket (elements)
+constexpr int kStageCap = SSSP_STAGE_CAP;  // block staging per L2 bucket (elements, a power of two >= 64)
 #ifndef SSSP_WINDOW_GUARD
 #define SSSP_WINDOW_GUARD 8
 #endif
@@ -269,7 +275,7 @@ __device__ __forceinline__ bool ahead(uint32_t w, uint32_t r) { return (int32_t)
 #define SSSP_FINE_CYCLES 0
 #endif
 #ifndef SSSP_BULK_REFILL
-#define SSSP_BULK_REFILL 1
+#define SSSP_BULK_REFILL 0
 #endif
 #ifndef SSSP_LF_STAGE
 #define SSSP_LF_STAGE 1
@@ -503,7 +509,8 @@ struct Worker {
     }
     __device__ __forceinline__ DistT* dist() const { return reinterpret_cast<DistT*>(P.dist); }
 
-    __device__ explicit Worker(const KParams& p) : P(p), lane(lane_id()), l0h(0), l0t(0), nfar(0), unc(0), dec(0) {
+    __device__ explicit Worker(const KParams& p)
+        : P(p), lane(lane_id()), l0h(0), l0t(0), nfar(0), unc(0), dec(0) {
         if (lane == 0)
             for (int i = 0; i < kStCount; i++) sst()[i] = 0;
 #pragma unroll

@@ -421,7 +421,7 @@ static void config_defaults(sssp_config* c) {
     c->split_arcs = 0;
     c->hub_bnum = 0;
     c->dedup = 0;
-    c->pending_marks = 1;
+    c->pending_marks = 0;
 }
 
 // Fills auto fields from the graph features (the prior of Section 3.5).

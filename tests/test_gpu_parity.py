@@ -100,7 +100,8 @@ def test_random_graphs_stress(seed):
     G = upload(g)
     c = cfg(l1_type=L1_ALL[seed % 4], l2_type=seed % 2, l1_cap=256, bmax=int(rng.choice([1, 2, 8, 32])),
             bnum=int(rng.choice([1, 2, 4])), split_arcs=32, hub_bnum=int(rng.choice([0, 1, 2])),
-            dedup=int(seed % 2), wb=int(rng.choice([0, 1, 4])), block_threads=int(rng.choice([256, 512, 1024])))
+            dedup=int(seed % 2), wb=int(rng.choice([0, 1, 4])), block_threads=int(rng.choice([256, 512, 1024])),
+            pending_marks=int(seed % 5 == 0))
     if wt == "u32":
         c.delta_u32 = int(rng.integers(1, 200))
     else:
