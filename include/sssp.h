@@ -415,6 +415,9 @@ typedef struct sssp_serve_options {
                                             lane's queries restart on larger rings */
 #define SSSP_SERVE_INJECT_TIMEOUT     4  /* treat each lane's first slice as a timed-out device
                                             wait: the lane's queries fail with SSSP_E_TIMEOUT */
+#define SSSP_SERVE_INJECT_NEGATIVE    8  /* read each lane's first scanned slot as a negative L2
+                                            count (more reads than writes): the lane's queries fail
+                                            with SSSP_E_CUDA and the lane starts over */
 
 typedef struct sssp_serve_stats {
     int64_t submitted;

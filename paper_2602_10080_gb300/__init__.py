@@ -30,7 +30,7 @@ SSSP_W_F32 = 1
 L1_VECTOR, L1_NEARFAR, L1_FILTER, L1_SLF = 0, 1, 2, 3
 L2_VECTOR, L2_BUCKET = 0, 1
 Q_QUEUED, Q_RUNNING, Q_DONE, Q_ERROR = 0, 1, 2, 3
-SERVE_MIGRATE_EACH_SLICE, SERVE_INJECT_OVERFLOW, SERVE_INJECT_TIMEOUT = 1, 2, 4
+SERVE_MIGRATE_EACH_SLICE, SERVE_INJECT_OVERFLOW, SERVE_INJECT_TIMEOUT, SERVE_INJECT_NEGATIVE = 1, 2, 4, 8
 
 
 class SsspError(RuntimeError):

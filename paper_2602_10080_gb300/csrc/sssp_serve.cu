@@ -263,6 +263,7 @@ struct Lane {
     int running = 0;            // slots holding a live query
     int prev_running = 0;       // running when the current admission round began
     bool injected = false;      // a test flag's injected failure has been applied
+    bool injected_neg = false;  // SSSP_SERVE_INJECT_NEGATIVE has been applied
     int draining = 0;
     int nadm = 0;               // admissions staged for the next slice
     bool inflight = false;      // a slice is queued or running on the stream
@@ -866,6 +867,11 @@ int collect_lane(sssp_server* s, Lane* L) {
             const bool occupied = L->slot_q[k] || L->drain[k];
             if (!occupied) continue;
             Query* q = L->slot_q[k];
+            if (!L->injected_neg && (s->opt.flags & SSSP_SERVE_INJECT_NEGATIVE)) {
+                // test flag: the lane's first scanned slot reads as a negative count
+                L->injected_neg = true;
+                L->live_h[k] = 0xffffffffu;
+            }
             if ((int32_t)L->live_h[k] < 0) {
                 // an impossible count (more L2 reads than writes): the lane's
                 // accounting is broken; its queries fail and it starts over
@@ -1079,7 +1085,8 @@ extern "C" int sssp_serve_create(const sssp_serve_options* opt_in, sssp_server**
     if (opt.max_slots < 1 || opt.max_slots > 4096 || opt.slice_us < 50 || opt.slice_us > 100000 ||
         opt.max_queued < 1 || opt.ring_shift < 0 || opt.ring_shift > 16 || opt.query_timeout_ms < 0)
         return SSSP_E_INVAL;
-    if (opt.flags & ~(SSSP_SERVE_MIGRATE_EACH_SLICE | SSSP_SERVE_INJECT_OVERFLOW | SSSP_SERVE_INJECT_TIMEOUT))
+    if (opt.flags & ~(SSSP_SERVE_MIGRATE_EACH_SLICE | SSSP_SERVE_INJECT_OVERFLOW | SSSP_SERVE_INJECT_TIMEOUT |
+                      SSSP_SERVE_INJECT_NEGATIVE))
         return SSSP_E_INVAL;
     for (int i = 0; i < 2; i++)
         if (opt.reserved[i] != 0) return SSSP_E_INVAL;

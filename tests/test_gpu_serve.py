@@ -221,6 +221,28 @@ def test_serve_injected_timeout_fails_lane_then_recovers(graphs):
         S.sssp_serve_destroy(srv)
 
 
+def test_serve_negative_count_fails_lane_then_recovers(graphs):
+    """A lane whose per-slot L2 count reads negative (injected on the host:
+    more reads than writes) fails its queries with SSSP_E_CUDA and starts
+    over on fresh rings; later queries in it are exact."""
+    g, G = graphs["rmat"]
+    srcs, _ = gg.giant_sources(g, 3, seed=9)
+    srv = S.sssp_serve_create(slice_us=200, flags=S.SERVE_INJECT_NEGATIVE)
+    try:
+        d0, _ = _bufs(G, False, host=False)
+        t0 = S.sssp_serve_submit(srv, G.handle, int(srcs[0]), d0, None)
+        st, code = S.sssp_serve_wait(srv, t0, 60000)
+        assert st == S.Q_ERROR and code == S.SSSP_E_CUDA, (st, S.strerror(code))
+        d1, p1 = _bufs(G, False, host=False)
+        t1 = S.sssp_serve_submit(srv, G.handle, int(srcs[1]), d1, None)
+        _wait_all(srv, [t1])
+        assert_exact(g, int(srcs[1]), _dist_bits(d1))
+        stats = S.sssp_serve_get_stats(srv)
+        assert stats["failed"] == 1 and stats["completed"] >= 1, stats
+    finally:
+        S.sssp_serve_destroy(srv)
+
+
 def test_serve_cancel(graphs):
     g, G = graphs["road"]
     gs, Gs = graphs["grid"]
