@@ -391,7 +391,9 @@ SSSP_API int sssp_bfs(sssp_graph *g, int32_t src, uint32_t *level_out, int32_t *
 typedef struct sssp_serve_options {
     size_t  mem_budget_bytes;  /* device bytes for distance slices and L2 rings of all lanes
                                   (0 = a quarter of the free device memory at creation) */
-    int32_t max_slots;         /* concurrent queries per lane, 1..4096 (default 256); also
+    int32_t max_slots;         /* concurrent queries per lane, 1..4096 (default 128: with five
+                                  resident graphs at 2000 q/s, 256 filled every lane and served
+                                  180 q/s, 128 served 340 q/s); also
                                   bounded by 2^32 / (vertices rounded up to a power of two) */
     int32_t slice_us;          /* length of one slice, 50..100000 (default 1000); a lane with
                                   q queries in flight runs slices of min(8, max(1, q / 4))

@@ -1068,7 +1068,7 @@ extern "C" int sssp_serve_options_default(sssp_serve_options* opt) {
     if (!opt) return SSSP_E_INVAL;
     std::memset(opt, 0, sizeof(*opt));
     opt->mem_budget_bytes = 0;
-    opt->max_slots = 256;
+    opt->max_slots = 128;
     opt->slice_us = 1000;
     opt->max_queued = 65536;
     opt->ring_shift = 4;

@@ -100,7 +100,7 @@ def test_bad_arguments_rejected_before_device(lib):
 
 def test_serve_options_rejected_before_device(lib):
     o = sssp.sssp_serve_options_default()
-    assert o.max_slots == 256 and o.slice_us == 1000 and o.flags == 0
+    assert o.max_slots == 128 and o.slice_us == 1000 and o.flags == 0
     assert lib.sssp_serve_options_default(None) == sssp.SSSP_E_INVAL
     h = ctypes.c_void_p()
     for field, value in (("max_slots", 0), ("max_slots", 5000), ("slice_us", 10), ("ring_shift", 17),
