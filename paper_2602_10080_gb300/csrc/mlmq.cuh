@@ -280,6 +280,9 @@ __device__ __forceinline__ bool ahead(uint32_t w, uint32_t r) { return (int32_t)
 #ifndef SSSP_LF_STAGE
 #define SSSP_LF_STAGE 1
 #endif
+#ifndef SSSP_SHADOW_OWNER
+#define SSSP_SHADOW_OWNER 0
+#endif
 #ifndef SSSP_SPEC_ROW
 #define SSSP_SPEC_ROW 0
 #endif
@@ -1940,6 +1943,27 @@ struct Worker {
                 uint32_t v = key_vertex(key);
                 rs = ld_row(P.row_ptr + v);
                 deg = ld_row(P.row_ptr + v + 1) - rs;
+#if SSSP_SHADOW_OWNER
+                if (v >= (uint32_t)P.n) {
+                    // a hub slice: when the hub has improved since the slice was
+                    // queued, relax from the hub's current distance and give the
+                    // slice that distance, so the hub's next relaxation of its
+                    // zero-weight links finds nothing to improve and queues no
+                    // second copy of the slice
+                    const uint32_t ow = (uint32_t)__ldg(P.owner + (v - (uint32_t)P.n));
+                    const size_t oidx = MQ ? (size_t)key_query(key) * (size_t)P.nv + ow : (size_t)ow;
+                    const uint32_t dO = dpart(ld_dist(dist() + oidx));
+                    if (dO < du) {
+                        du = dO;
+                        el.y = dO;
+                        if (PRED == 0)
+                            red_min(reinterpret_cast<uint32_t*>(dist()) + dist_index(key), dO);
+                        else
+                            red_min(reinterpret_cast<unsigned long long*>(dist()) + dist_index(key),
+                                    ((unsigned long long)dO << 32) | ow);
+                    }
+                }
+#endif
             }
 #endif
         }
