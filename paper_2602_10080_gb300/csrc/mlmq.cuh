@@ -281,7 +281,7 @@ __device__ __forceinline__ bool ahead(uint32_t w, uint32_t r) { return (int32_t)
 #define SSSP_LF_STAGE 1
 #endif
 #ifndef SSSP_SHADOW_OWNER
-#define SSSP_SHADOW_OWNER 0
+#define SSSP_SHADOW_OWNER 1
 #endif
 #ifndef SSSP_SPEC_ROW
 #define SSSP_SPEC_ROW 0
