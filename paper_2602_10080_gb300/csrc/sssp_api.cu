@@ -1190,11 +1190,13 @@ extern "C" int sssp_graph_create(const int32_t* row_ptr, const int32_t* col_idx,
         }
         f.symmetric = -1;
         f.has_zero_w = hacc.zero_w ? 1 : 0;
-        rc = build_layout(g, rp0, adj0, kDefaultSplit, s);
-        g->layout_req = kDefaultSplit;
-        f.shadows = g->nv - g->n;
-        // the graph's default configuration: the feature prior (Section 3.5)
+        // the graph's default configuration: the feature prior (Section 3.5); its hub
+        // split threshold gives the initial layout
         g->defaults = prior_config(g);
+        const int32_t split0 = g->defaults.split_arcs ? g->defaults.split_arcs : kDefaultSplit;
+        rc = build_layout(g, rp0, adj0, split0, s);
+        g->layout_req = split0;
+        f.shadows = g->nv - g->n;
         if (rc == SSSP_OK) {
             rp0 = nullptr;  // owned by the graph now (or freed by the relayout)
             adj0 = nullptr;

@@ -52,6 +52,10 @@ sssp_config prior_config(const Graph* g) {
             c.near_deltas = 1.0f;
             c.bnum = 16;
             c.claim = 8;   // many small buckets of work: fewer, larger L2 reads
+            // hub slices of 512 arcs: with each slice relaxed from its hub's current
+            // distance, R-MAT-22 took 6.8 ms against 8.0 ms with 1024 (relaxations
+            // 237M -> 178M; 384: 7.0, 768: 6.9, 256: 8.3 ms) on GB300
+            c.split_arcs = 512;
             break;
         case kMesh:
             c.l1_type = SSSP_L1_FILTER;
@@ -76,11 +80,16 @@ sssp_config prior_config(const Graph* g) {
     resolve_auto(g, &c);
     if (family_of(f) == kRoad && f.n > (1 << 22)) {
         // a large road-shaped graph advances as a thin wavefront whose reads are bound by L2
-        // claims: wider buckets give each claim more work.  On the 4096^2 road graph on GB300,
-        // 4x the general width with 8 active buckets took 33 ms against 44 ms (2x: 39, 8x:
-        // 58 ms); on grids of 256^2 and 1024^2 vertices the same rule was 15% and 3% slower
+        // claims: wider buckets give each claim more work, and fewer warps contend for the
+        // claims.  On the 4096^2 road graph on GB300, 4x the general width with 8 active
+        // buckets took 33 ms against 44 ms (2x: 39, 8x: 58 ms); one block per SM with 16 shards
+        // per bucket and 4 refilling warps per block then took 21 ms.  On grids of 256^2 and
+        // 1024^2 vertices the wider buckets were 15% and 3% slower, hence the size gate
         if (g->wtype == SSSP_W_F32) c.delta_f32 *= 4.0f;
         else c.delta_u32 = (uint32_t)std::min<uint64_t>(4000000000ull, (uint64_t)c.delta_u32 * 4u);
+        c.blocks_per_sm = 1;
+        c.shards = 16;
+        c.refillers = 4;
     }
     if (family_of(f) == kPowerLaw) {
         // a quarter of the general width with 16 active buckets (the same

@@ -115,10 +115,11 @@ def test_random_graphs_stress(seed):
         assert (shadows > 0) == (max_deg > 32), (shadows, max_deg)
         d2, _ = gpu_solve(G, src, pred=False, config=c)
         np.testing.assert_array_equal(d2, d)
-    # back to the default threshold: the layout is rebuilt again, same results
+    # back to the graph's own configuration: the layout is rebuilt with its threshold
     d3, p3 = gpu_solve(G, int(src), pred=True)
     assert_exact(g, int(src), d3, p3)
-    assert (G.features()["shadows"] > 0) == (max_deg > 1024)
+    own = G.autotune(None, 0).split_arcs or 1024
+    assert (G.features()["shadows"] > 0) == (max_deg > own)
 
 
 def test_rmat_f32_exact_and_close_to_f64():
@@ -145,7 +146,11 @@ def test_heavy_vertex_shadows():
     edges += [(777, v, 1 + v % 13) for v in range(1000, 4000)]
     g = gg.from_edges(n, edges)
     G = upload(g)
-    assert G.features()["shadows"] == 196 + 3
+    # every vertex above the graph's split threshold becomes ceil(arcs / threshold) shadows
+    split = G.autotune(None, 0).split_arcs or 1024
+    deg = np.diff(g.row_ptr)
+    assert G.features()["shadows"] == int(sum(-(-d // split) for d in deg if d > split))
+    assert G.features()["shadows"] >= 199
     for src in (0, 777, 5):
         for ma in (32, 4096):
             d, p = gpu_solve(G, src, pred=True, config=cfg(max_arcs=ma))
