@@ -618,8 +618,9 @@ def main():
                    "n": g.n, "m": g.m, "giant": giant, "l2_flush": l2_note,
                    "l2_residency": l2_res,
                    "queue": {k: v for k, v in tuned.as_dict().items()
-                             if k in ("l1_type", "l2_type", "delta_u32", "bnum", "bmax", "wb",
-                                      "filter_deltas", "th_heavy", "block_threads")},
+                             if k in ("l1_type", "l2_type", "delta_u32", "bnum", "bmax", "wb", "claim",
+                                      "filter_deltas", "th_heavy", "block_threads", "split_arcs",
+                                      "hub_bnum")},
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": round(e2e_value, 3), "unit": "GTEPS", "h2d_bytes_per_step": 4,
                 "d2h_bytes_per_step": 8 * g.n},
