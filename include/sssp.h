@@ -144,7 +144,12 @@ typedef struct sssp_config {
                               are the same; queue traffic drops, but the extra atomic per
                               improvement costs more on the measured graphs (default 0 = queue
                               every improvement) */
-    int32_t reserved;      /* must be zero */
+    int32_t direct_buckets; /* with block staging: a heavy-arc write whose bucket is among the first
+                              direct_buckets buckets of the window skips the staging and goes to
+                              L2 at once, and a refill first sends the staged elements of those
+                              buckets to L2 (0..32; default 2).  0 stages every write until a
+                              full chunk or until the block runs dry: fuller chunks, later
+                              publication */
 } sssp_config;
 
 /* Graph features of Table 2 (Section 3.5), computed at creation. */

@@ -49,11 +49,11 @@ class sssp_config(ctypes.Structure):
         ("stage", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
         ("timeout_ms", ctypes.c_int32), ("l2_only", ctypes.c_int32), ("split_arcs", ctypes.c_int32),
         ("hub_bnum", ctypes.c_int32), ("dedup", ctypes.c_int32), ("pending_marks", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("direct_buckets", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class sssp_serve_options(ctypes.Structure):

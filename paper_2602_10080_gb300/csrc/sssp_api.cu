@@ -422,6 +422,7 @@ static void config_defaults(sssp_config* c) {
     c->hub_bnum = 0;
     c->dedup = 0;
     c->pending_marks = 0;
+    c->direct_buckets = 2;
 }
 
 // Fills auto fields from the graph features (the prior of Section 3.5).
@@ -499,7 +500,7 @@ int validate_config(const sssp_config* c) {
     if (c->split_arcs != 0 && (c->split_arcs < 32 || c->split_arcs > (1 << 30))) return SSSP_E_INVAL;
     if (c->hub_bnum < 0 || c->hub_bnum > 32 || c->dedup < 0 || c->dedup > 1) return SSSP_E_INVAL;
     if (c->pending_marks < 0 || c->pending_marks > 1) return SSSP_E_INVAL;
-    if (c->reserved != 0) return SSSP_E_INVAL;
+    if (c->direct_buckets < 0 || c->direct_buckets > 32) return SSSP_E_INVAL;
     return SSSP_OK;
 }
 
@@ -546,6 +547,7 @@ int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, 
     // hub rings need two shard halves and a bucketed L2
     P.hub_bnum = (cfg.shards >= 2 && cfg.bmax > 1 && !cfg.l2_only) ? cfg.hub_bnum : 0;
     P.dedup = cfg.dedup;
+    P.direct = (uint32_t)cfg.direct_buckets;
     P.bnum = std::min(cfg.bnum, cfg.bmax);
     P.bmax = cfg.bmax;
     P.l1_type = cfg.l1_type;

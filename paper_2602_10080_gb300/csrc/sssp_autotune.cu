@@ -56,6 +56,10 @@ sssp_config prior_config(const Graph* g) {
             // distance, R-MAT-22 took 6.8 ms against 8.0 ms with 1024 (relaxations
             // 237M -> 178M; 384: 7.0, 768: 6.9, 256: 8.3 ms) on GB300
             c.split_arcs = 512;
+            // every write is staged until its bucket fills a chunk: on R-MAT-22 on GB300
+            // 6.2 ms against 6.7 ms with the first two buckets written directly, and the
+            // 256-query batch on R-MAT-20 289 ms against 297 ms
+            c.direct_buckets = 0;
             break;
         case kMesh:
             c.l1_type = SSSP_L1_FILTER;
@@ -232,6 +236,12 @@ extern "C" int sssp_autotune(sssp_graph* gh, const int32_t* srcs, int32_t nsrc, 
             sssp_config c = best;
             if (c.hub_bnum == hb) continue;
             c.hub_bnum = hb;
+            cands.push_back(c);
+        }
+        for (int db : {0, 2}) {
+            sssp_config c = best;
+            if (c.direct_buckets == db || !c.stage) continue;
+            c.direct_buckets = db;
             cands.push_back(c);
         }
         if (g->feat.max_deg > 256.0) {
