@@ -63,7 +63,7 @@ constexpr int kChunk = 32;          // elements per L2 chunk
 #define SSSP_STAGE_CAP 64
 #endif
 constexpr int kFarCap = SSSP_FAR_CAP;  // per-warp far staging (elements)
-constexpr int kMaxClaim = 8;        // chunks per L2 claim (upper bound)
+constexpr int kMaxClaim = 16;       // chunks per L2 claim (upper bound, a power of two)
 constexpr int kStageCap = SSSP_STAGE_CAP;  // block staging per L2 bucket (elements, a power of two >= 64)
 #ifndef SSSP_WINDOW_GUARD
 #define SSSP_WINDOW_GUARD 8
@@ -293,18 +293,6 @@ __device__ __forceinline__ bool ahead(uint32_t w, uint32_t r) { return (int32_t)
 #ifndef SSSP_NOINLINE
 #define SSSP_NOINLINE __noinline__
 #endif
-#ifndef SSSP_PARAM_SMEM
-#define SSSP_PARAM_SMEM 1
-#endif
-#ifndef SSSP_GRID_CONST
-#define SSSP_GRID_CONST SSSP_PARAM_SMEM
-#endif
-#ifndef SSSP_PRM_SYMBOL
-#define SSSP_PRM_SYMBOL 0
-#endif
-#ifndef SSSP_STAGE_PAR
-#define SSSP_STAGE_PAR 1
-#endif
 #ifndef SSSP_CLAIM_TRIES
 #define SSSP_CLAIM_TRIES 4
 #endif
@@ -451,10 +439,9 @@ struct BlockShared {
     unsigned long long next_sample;
     uint32_t nsamples;
     uint32_t busy;                // warps of the block holding a batch (sampling only)
-#if SSSP_PARAM_SMEM
     KParams params;               // the launch parameters, read by the workers from here
-#endif
 };
+static_assert(sizeof(KParams) % 4 == 0, "the prologue copies KParams in 4-byte words");
 
 // ------------------------------------------------------------- watchdog --
 
@@ -499,17 +486,7 @@ struct Worker {
     using DistT = typename std::conditional<PRED == 0, uint32_t, unsigned long long>::type;
     using A = Arith<WT>;
 
-#if SSSP_PRM_SYMBOL
-    // the launch parameters, copied to shared memory by the kernel prologue:
-    // addressed from the shared-memory symbol, so every field read is a
-    // shared-memory load at a fixed offset
-    __device__ __forceinline__ const KParams& prm() const {
-        return reinterpret_cast<const BlockShared*>(mlmq_smem)->params;
-    }
-#else
-    const KParams& P;
-    __device__ __forceinline__ const KParams& prm() const { return P; }
-#endif
+    const KParams& P;   // the launch parameters (the block's shared-memory copy)
     uint32_t lane;
 
     // L0 ring
@@ -526,31 +503,26 @@ struct Worker {
     __device__ __forceinline__ BlockShared* S() const { return reinterpret_cast<BlockShared*>(mlmq_smem); }
     // this warp's 32-element staging area
     __device__ __forceinline__ uint2* scratch() const {
-        return reinterpret_cast<uint2*>(mlmq_smem + prm().scratch_off) + warp_id() * 32u;
+        return reinterpret_cast<uint2*>(mlmq_smem + P.scratch_off) + warp_id() * 32u;
     }
     // this warp's far staging (kFarCap elements)
     __device__ __forceinline__ uint2* farbuf() const {
-        return reinterpret_cast<uint2*>(mlmq_smem + prm().far_off) + warp_id() * (uint32_t)kFarCap;
+        return reinterpret_cast<uint2*>(mlmq_smem + P.far_off) + warp_id() * (uint32_t)kFarCap;
     }
     // block staging, kStageCap elements per L2 bucket ring index
-    __device__ __forceinline__ uint2* stg() const { return reinterpret_cast<uint2*>(mlmq_smem + prm().stage_off); }
+    __device__ __forceinline__ uint2* stg() const { return reinterpret_cast<uint2*>(mlmq_smem + P.stage_off); }
     // block L1 buffer
     __device__ __forceinline__ volatile uint2* L1() const {
-        return reinterpret_cast<volatile uint2*>(mlmq_smem + prm().l1_off);
+        return reinterpret_cast<volatile uint2*>(mlmq_smem + P.l1_off);
     }
     // statistics of this warp (lane 0 updates)
     __device__ __forceinline__ unsigned long long* sst() const {
-        return reinterpret_cast<unsigned long long*>(mlmq_smem + prm().stat_off) + warp_id() * (uint32_t)kStCount;
+        return reinterpret_cast<unsigned long long*>(mlmq_smem + P.stat_off) + warp_id() * (uint32_t)kStCount;
     }
-    __device__ __forceinline__ DistT* dist() const { return reinterpret_cast<DistT*>(prm().dist); }
+    __device__ __forceinline__ DistT* dist() const { return reinterpret_cast<DistT*>(P.dist); }
 
     __device__ explicit Worker(const KParams& p)
-#if SSSP_PRM_SYMBOL
-        : lane(lane_id()), l0h(0), l0t(0), nfar(0), unc(0), dec(0) {
-        (void)p;
-#else
         : P(p), lane(lane_id()), l0h(0), l0t(0), nfar(0), unc(0), dec(0) {
-#endif
         if (lane == 0)
             for (int i = 0; i < kStCount; i++) sst()[i] = 0;
 #pragma unroll
@@ -565,24 +537,24 @@ struct Worker {
     __device__ __forceinline__ bool expired() const { return gtime() > S()->deadline; }
 
     __device__ __forceinline__ bool aborted() const {
-        return ld_volatile_int(&prm().ctrl->error) != 0 || ld_volatile_int(&prm().ctrl->finished) != 0;
+        return ld_volatile_int(&P.ctrl->error) != 0 || ld_volatile_int(&P.ctrl->finished) != 0;
     }
 
-    // debug trace of where each lane is (no-op unless prm().trace is set)
+    // debug trace of where each lane is (no-op unless P.trace is set)
     __device__ __forceinline__ void mark(uint32_t code, uint32_t iter = 0) const {
-        if (prm().trace) {
+        if (P.trace) {
             const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
-            *(volatile unsigned long long*)(prm().trace + gt) =
+            *(volatile unsigned long long*)(P.trace + gt) =
                 ((unsigned long long)code << 48) | (unsigned long long)(iter & 0xffffffffffffull);
             __threadfence_system();
         }
     }
 
     // ---- element helpers
-    __device__ __forceinline__ uint32_t key_query(uint32_t key) const { return MQ ? key >> prm().vbits : 0u; }
-    __device__ __forceinline__ uint32_t key_vertex(uint32_t key) const { return MQ ? key & prm().vmask : key; }
+    __device__ __forceinline__ uint32_t key_query(uint32_t key) const { return MQ ? key >> P.vbits : 0u; }
+    __device__ __forceinline__ uint32_t key_vertex(uint32_t key) const { return MQ ? key & P.vmask : key; }
     __device__ __forceinline__ size_t dist_index(uint32_t key) const {
-        return MQ ? (size_t)key_query(key) * (size_t)prm().nv + key_vertex(key) : (size_t)key;
+        return MQ ? (size_t)key_query(key) * (size_t)P.nv + key_vertex(key) : (size_t)key;
     }
     static __device__ __forceinline__ uint32_t dpart(uint32_t w) { return w; }
     static __device__ __forceinline__ uint32_t dpart(unsigned long long w) { return (uint32_t)(w >> 32); }
@@ -605,7 +577,7 @@ struct Worker {
             unsigned long long old = atomicCAS(&S()->acct, v, 0ull);
             if (old == v) {
                 fence_gpu();
-                atomicAdd(&prm().ctrl->done, (unsigned long long)(uint32_t)v);
+                atomicAdd(&P.ctrl->done, (unsigned long long)(uint32_t)v);
                 return;
             }
             v = old;
@@ -642,7 +614,7 @@ struct Worker {
             for (;;) {
                 if (*(volatile int*)word == 0 && atomicCAS(word, 0, 1) == 0) break;
                 if ((++spins & 255u) == 0 && expired()) {
-                    raise_error(prm().ctrl, kErrTimeout, 1, 0);
+                    raise_error(P.ctrl, kErrTimeout, 1, 0);
                     ok = 0;
                     break;
                 }
@@ -671,31 +643,31 @@ struct Worker {
 
     // ---- L2: sharded bucket rings -----------------------------------------
     __device__ __forceinline__ unsigned long long window() const {
-        return ld_acquire64(&prm().ctrl->window);
+        return ld_acquire64(&P.ctrl->window);
     }
     __device__ __forceinline__ uint32_t home_shard() const {
-        return (blockIdx.x + (threadIdx.x >> 5)) & (uint32_t)(prm().shards - 1);
+        return (blockIdx.x + (threadIdx.x >> 5)) & (uint32_t)(P.shards - 1);
     }
     // The shard an element is written to: its home shard, or with hub rings
     // (hub_bnum > 0) the lower half of the shards for ordinary vertices and
     // the upper half for shadow vertices.
     __device__ __forceinline__ uint32_t write_shard(bool shadow) const {
-        if (prm().hub_bnum <= 0) return home_shard();
-        const uint32_t half = (uint32_t)prm().shards >> 1;
+        if (P.hub_bnum <= 0) return home_shard();
+        const uint32_t half = (uint32_t)P.shards >> 1;
         return (shadow ? half : 0u) + (home_shard() & (half - 1u));
     }
     __device__ __forceinline__ bool hub_ring(uint32_t shard) const {
-        return prm().hub_bnum > 0 && shard >= ((uint32_t)prm().shards >> 1);
+        return P.hub_bnum > 0 && shard >= ((uint32_t)P.shards >> 1);
     }
 
     // Serving: adds `sign` per valid element to its query's L2 count, one
     // atomic per distinct query of the warp.  At the end of a slice every
     // element is in L2, so a count of zero means the query is complete.
     __device__ __forceinline__ void count_live(bool valid, uint32_t key, int sign) {
-        if (!MQ || !prm().qlive) return;
+        if (!MQ || !P.qlive) return;
         const uint32_t q = valid ? key_query(key) : 0xffffffffu;
         const uint32_t grp = __match_any_sync(kFull, q);
-        if (valid && (grp & lanemask_lt()) == 0u) atomicAdd(prm().qlive + q, sign * __popc(grp));
+        if (valid && (grp & lanemask_lt()) == 0u) atomicAdd(P.qlive + q, sign * __popc(grp));
     }
 
     // Writes the valid lanes' elements to the L2 bucket of their distance
@@ -715,7 +687,7 @@ struct Worker {
         const int total = __popc(vm);
         unsigned long long win = 0;
         if (lane == 0) {
-            atomicAdd(&prm().ctrl->reserve, (unsigned long long)total);
+            atomicAdd(&P.ctrl->reserve, (unsigned long long)total);
             win = window();
         }
         win = __shfl_sync(kFull, win, 0);
@@ -723,14 +695,14 @@ struct Worker {
         // absolute bucket (clamp_bucket: beyond the window's reach -> its far end)
         uint32_t ab = valid ? abs_bucket(e.x, e.y) : W;
         ab = clamp_bucket(ab, W);
-        const uint32_t b = ab % (uint32_t)prm().bmax;
+        const uint32_t b = ab % (uint32_t)P.bmax;
         const uint32_t below = __reduce_min_sync(kFull, valid ? ab : 0xffffffffu);
-        const bool shadow = valid && key_vertex(e.x) >= (uint32_t)prm().n;
+        const bool shadow = valid && key_vertex(e.x) >= (uint32_t)P.n;
         const uint32_t shard = write_shard(shadow);
         const uint32_t gkey = !valid ? 0xffffffffu : (shadow ? (0x80000000u | lane) : b);
         const uint32_t grp = __match_any_sync(kFull, gkey);
         const bool leader = valid && (grp & lanemask_lt()) == 0u;
-        uint32_t t = 0, ring = b * (uint32_t)prm().shards + shard;
+        uint32_t t = 0, ring = b * (uint32_t)P.shards + shard;
         int okw = 1;
         if (leader) {
             // take a ticket on the first ring (from b towards the window end)
@@ -738,30 +710,30 @@ struct Worker {
             // only delays it (results are order independent).
             uint32_t tries = 0, bucket = b;
             for (;;) {
-                uint32_t* wtp = prm().l2.wt + (size_t)ring * 32;
-                uint32_t* rtp = prm().l2.rt + (size_t)ring * 32;
+                uint32_t* wtp = P.l2.wt + (size_t)ring * 32;
+                uint32_t* rtp = P.l2.rt + (size_t)ring * 32;
                 // read r before w (acquire) so w - r over-estimates the occupancy
                 const uint32_t r0 = ld_acquire(rtp);
                 const uint32_t w0 = ld_relaxed(wtp);
-                if (w0 - r0 + prm().l2.margin < prm().l2.nch) {
+                if (w0 - r0 + P.l2.margin < P.l2.nch) {
                     t = atomicAdd(wtp, 1u);
                     break;
                 }
-                if (++tries >= (uint32_t)prm().bmax) {
-                    raise_error(prm().ctrl, kErrOverflow, 2, (int)bucket);
+                if (++tries >= (uint32_t)P.bmax) {
+                    raise_error(P.ctrl, kErrOverflow, 2, (int)bucket);
                     okw = 0;
                     break;
                 }
-                bucket = (bucket + 1u) % (uint32_t)prm().bmax;
-                ring = bucket * (uint32_t)prm().shards + shard;
+                bucket = (bucket + 1u) % (uint32_t)P.bmax;
+                ring = bucket * (uint32_t)P.shards + shard;
             }
             if (okw) {
                 // wait until the chunk slot of ticket t is free (normally immediate)
-                uint32_t* sp = prm().l2.seq + (size_t)ring * prm().l2.nch + (t & (prm().l2.nch - 1u));
+                uint32_t* sp = P.l2.seq + (size_t)ring * P.l2.nch + (t & (P.l2.nch - 1u));
                 uint32_t spins = 0;
                 while (ld_acquire(sp) != t) {
                     if ((++spins & 255u) == 0 && expired()) {
-                        raise_error(prm().ctrl, kErrTimeout, 3, (int)ring);
+                        raise_error(P.ctrl, kErrTimeout, 3, (int)ring);
                         okw = 0;
                         break;
                     }
@@ -776,20 +748,20 @@ struct Worker {
         okw = __shfl_sync(kFull, okw, ldr);
         if (!__all_sync(kFull, okw || !valid)) return total;
         count_live(valid, e.x, 1);
-        const size_t slot = (size_t)ring * prm().l2.nch + (t & (prm().l2.nch - 1u));
-        if (valid) prm().l2.data[slot * kChunk + __popc(grp & lanemask_lt())] = e;
+        const size_t slot = (size_t)ring * P.l2.nch + (t & (P.l2.nch - 1u));
+        if (valid) P.l2.data[slot * kChunk + __popc(grp & lanemask_lt())] = e;
         __syncwarp();
         if (leader) {
-            prm().l2.cnt[slot] = (uint32_t)__popc(grp);
+            P.l2.cnt[slot] = (uint32_t)__popc(grp);
             fence_gpu();
-            st_release(prm().l2.seq + slot, t + 1u);
+            st_release(P.l2.seq + slot, t + 1u);
         }
         stat(kStChunks, (unsigned long long)__popc(__ballot_sync(kFull, leader)));
         __syncwarp();
         // written below the window: work held in the local queues (L0/L1),
         // which the window does not see, has smaller distances than the L2
         // front; pull the window back so readers see these buckets first
-        if (lane == 0 && below < W) atomicMin(&prm().ctrl->window, (unsigned long long)below);
+        if (lane == 0 && below < W) atomicMin(&P.ctrl->window, (unsigned long long)below);
         stat(kStPullBack, below < W ? 1u : 0u);
         stat(kStLowWrite, (unsigned long long)__popc(__ballot_sync(kFull, valid && ab < 2u)));
         stat(kCyL2Write, (unsigned long long)(clock64() - cw0));
@@ -811,16 +783,16 @@ struct Worker {
         if (lane == 0) win = window();
         win = __shfl_sync(kFull, win, 0);
         const uint32_t W = (uint32_t)win;
-        const uint32_t S_ = (uint32_t)prm().shards, per = 32u / S_;
+        const uint32_t S_ = (uint32_t)P.shards, per = 32u / S_;
         const uint32_t home = home_shard();
-        for (uint32_t r0 = 0; r0 < (uint32_t)prm().bmax; r0 += per) {
+        for (uint32_t r0 = 0; r0 < (uint32_t)P.bmax; r0 += per) {
             const uint32_t rel = r0 + lane / S_;
-            const bool probe = rel < (uint32_t)prm().bmax;
-            const uint32_t ring = ((W + rel) % (uint32_t)prm().bmax) * S_ + ((home + lane) & (S_ - 1u));
+            const bool probe = rel < (uint32_t)P.bmax;
+            const uint32_t ring = ((W + rel) % (uint32_t)P.bmax) * S_ + ((home + lane) & (S_ - 1u));
             uint32_t r = 0, w = 0;
             if (probe) {
-                r = ld_relaxed(prm().l2.rt + (size_t)ring * 32);
-                w = ld_relaxed(prm().l2.wt + (size_t)ring * 32);
+                r = ld_relaxed(P.l2.rt + (size_t)ring * 32);
+                w = ld_relaxed(P.l2.wt + (size_t)ring * 32);
             }
             const bool ne = probe && ahead(w, r);
             const uint32_t nonempty = __ballot_sync(kFull, ne);
@@ -828,26 +800,26 @@ struct Worker {
             const int first = __ffs(nonempty) - 1;
             const uint32_t first_rel = r0 + (uint32_t)first / S_;
             if (first_rel > 0 && lane == 0)
-                if (atomicCAS(&prm().ctrl->window, win, (unsigned long long)(W + first_rel)) == win) sst()[kStAdvance]++;
+                if (atomicCAS(&P.ctrl->window, win, (unsigned long long)(W + first_rel)) == win) sst()[kStAdvance]++;
             // candidates: non-empty rings of buckets within bnum of the first
             // one; hub rings only within hub_bnum of it (a hub slice is
             // relaxed once its distance is near the front, so it is rarely
             // relaxed again)
-            const uint32_t lim = hub_ring((home + lane) & (S_ - 1u)) ? (uint32_t)prm().hub_bnum : (uint32_t)prm().bnum;
+            const uint32_t lim = hub_ring((home + lane) & (S_ - 1u)) ? (uint32_t)P.hub_bnum : (uint32_t)P.bnum;
             uint32_t cand = __ballot_sync(kFull, ne && rel < first_rel + lim);
             while (cand) {
                 int c = __ffs(cand) - 1;
                 uint32_t got = 0, t = 0;
                 if (lane == (uint32_t)c) {
                     uint32_t rr = r;
-                    uint32_t* rtp = prm().l2.rt + (size_t)ring * 32;
+                    uint32_t* rtp = P.l2.rt + (size_t)ring * 32;
                     for (int k = 0; k < SSSP_CLAIM_TRIES && ahead(w, rr); k++) {
                         uint32_t avail = w - rr;
                         uint32_t take = avail < want ? avail : want;
                         uint32_t old = atomicCAS(rtp, rr, rr + take);
                         if (old == rr) { got = take; t = rr; break; }
                         rr = old;
-                        w = ld_relaxed(prm().l2.wt + (size_t)ring * 32);
+                        w = ld_relaxed(P.l2.wt + (size_t)ring * 32);
                     }
                     if (!got) atomicAdd((unsigned long long*)&sst()[kStCasFail], 1ull);
                 }
@@ -872,18 +844,18 @@ struct Worker {
         int ok = 1;
         mark(4);
         if (lane < got) {
-            const size_t slot = (size_t)ring * prm().l2.nch + ((t + lane) & (prm().l2.nch - 1u));
+            const size_t slot = (size_t)ring * P.l2.nch + ((t + lane) & (P.l2.nch - 1u));
             uint32_t spins = 0;
-            while (ld_acquire(prm().l2.seq + slot) != t + lane + 1u) {
+            while (ld_acquire(P.l2.seq + slot) != t + lane + 1u) {
                 if ((++spins & 255u) == 0 && expired()) {
-                    raise_error(prm().ctrl, kErrTimeout, 5, (int)ring);
+                    raise_error(P.ctrl, kErrTimeout, 5, (int)ring);
                     ok = 0;
                     break;
                 }
                 __nanosleep(32);
             }
             if (spins) atomicAdd(&sst()[kStWaitSpin], (unsigned long long)spins);
-            if (ok) cnt = prm().l2.cnt[slot];
+            if (ok) cnt = P.l2.cnt[slot];
         }
         okr = __all_sync(kFull, ok != 0);
         return cnt;
@@ -891,20 +863,20 @@ struct Worker {
 
     // Reads chunk t + j (count c) into the lanes and frees its slot.
     __device__ void l2_read_chunk(uint32_t ring, uint32_t tj, uint32_t c, bool& valid, uint2& e) {
-        const size_t slot = (size_t)ring * prm().l2.nch + (tj & (prm().l2.nch - 1u));
+        const size_t slot = (size_t)ring * P.l2.nch + (tj & (P.l2.nch - 1u));
         valid = lane < c;
-        if (valid) e = prm().l2.data[slot * kChunk + lane];
+        if (valid) e = P.l2.data[slot * kChunk + lane];
         count_live(valid, e.x, -1);
         __syncwarp();
         if (lane == 0) {
             fence_gpu();
-            st_release(prm().l2.seq + slot, tj + prm().l2.nch);
+            st_release(P.l2.seq + slot, tj + P.l2.nch);
         }
         __syncwarp();
     }
 
     // ---- L1 ------------------------------------------------------------------
-    __device__ __forceinline__ uint32_t l1_mask() const { return (uint32_t)prm().l1_cap - 1u; }
+    __device__ __forceinline__ uint32_t l1_mask() const { return (uint32_t)P.l1_cap - 1u; }
 
     // Places the valid elements (K per lane) into L1 under the block lock, per
     // the L1 policy; elements that do not fit or are filtered out get their
@@ -913,8 +885,8 @@ struct Worker {
     template <int K>
     __device__ void l1_place(uint2 (&e)[K], bool (&valid)[K], bool (&out)[K], uint32_t fthr,
                              int count_add) {
-        const int type = prm().l1_type;
-        const uint32_t cap = (uint32_t)prm().l1_cap;
+        const int type = P.l1_type;
+        const uint32_t cap = (uint32_t)P.l1_cap;
         if (type == 1) {
             // near-far: two rings of cap/2
             const uint32_t half = cap >> 1;
@@ -984,7 +956,7 @@ struct Worker {
                 // with admission offsets (serving) the filter compares
                 // absolute buckets: fthr then holds the last bucket kept
                 bool want = valid[k] &&
-                            (type != 2 || (MQ && prm().qoff ? abs_bucket(e[k].x, e[k].y) <= fthr : e[k].y <= fthr));
+                            (type != 2 || (MQ && P.qoff ? abs_bucket(e[k].x, e[k].y) <= fthr : e[k].y <= fthr));
                 uint32_t wm = __ballot_sync(kFull, want);
                 uint32_t h = sread(&S()->head), t = sread(&S()->tail);
                 uint32_t space = cap - (t - h);
@@ -1009,8 +981,8 @@ struct Worker {
     // Moves everything in L1 to L2 (periodic flush of L1V, Section 3.4).
     // Called with the lock held.
     __device__ void l1_flush_locked() {
-        const uint32_t cap = (uint32_t)prm().l1_cap;
-        if (prm().l1_type == 1) {
+        const uint32_t cap = (uint32_t)P.l1_cap;
+        if (P.l1_type == 1) {
             const uint32_t half = cap >> 1;
             for (int rg = 0; rg < 2; rg++) {
                 uint32_t* hp = rg ? &S()->fhead : &S()->head;
@@ -1053,11 +1025,11 @@ struct Worker {
     // head (bounded by tail) and withdraw from each once it is full.  Both
     // waits are on warps that are already inside the same operation, so they
     // are short; they are bounded by the deadline.
-    __device__ __forceinline__ bool l1_lockfree() const { return prm().l1_type == 0 || prm().l1_type == 2; }
+    __device__ __forceinline__ bool l1_lockfree() const { return P.l1_type == 0 || P.l1_type == 2; }
 
     template <int K>
     __device__ void l1_write_lf(uint2 (&e)[K], bool (&valid)[K], int count_add, uint32_t fthr) {
-        const uint32_t cap = (uint32_t)prm().l1_cap;
+        const uint32_t cap = (uint32_t)P.l1_cap;
         // the elements become visible to other warps: count them first
         if (lane == 0 && count_add != 0)
             atomicAdd(&S()->acct, ((unsigned long long)(uint32_t)count_add) << 32);
@@ -1065,8 +1037,8 @@ struct Worker {
         bool out[K];
 #pragma unroll
         for (int k = 0; k < K; k++) {
-            const bool want = valid[k] && (prm().l1_type != 2 ||
-                                           (MQ && prm().qoff ? abs_bucket(e[k].x, e[k].y) <= fthr : e[k].y <= fthr));
+            const bool want = valid[k] && (P.l1_type != 2 ||
+                                           (MQ && P.qoff ? abs_bucket(e[k].x, e[k].y) <= fthr : e[k].y <= fthr));
             const uint32_t wm = __ballot_sync(kFull, want);
             out[k] = valid[k] && !want;
             if (!wm) continue;
@@ -1096,7 +1068,7 @@ struct Worker {
                 uint32_t spins = 0;
                 while (!slot_try_put(slot, e[k])) {
                     if ((++spins & 255u) == 0 && expired()) {
-                        raise_error(prm().ctrl, kErrTimeout, 10, 0);
+                        raise_error(P.ctrl, kErrTimeout, 10, 0);
                         ok = 0;
                         break;
                     }
@@ -1131,7 +1103,7 @@ struct Worker {
             uint2 x = make_uint2(kEmptyKey, 0u);
             while (!slot_try_take(slot, x)) {
                 if ((++spins & 255u) == 0 && expired()) {
-                    raise_error(prm().ctrl, kErrTimeout, 11, 0);
+                    raise_error(P.ctrl, kErrTimeout, 11, 0);
                     break;
                 }
             }
@@ -1150,24 +1122,24 @@ struct Worker {
     __device__ void l1_write(uint2 (&e)[K], bool (&valid)[K], int count_add, bool filter = true) {
         const long long c0 = clock64();
         uint32_t fthr = kInfU32;
-        if (prm().l1_type == 2 && filter) {
+        if (P.l1_type == 2 && filter) {
             unsigned long long win = 0;
             if (lane == 0) win = window();
             win = __shfl_sync(kFull, win, 0);
-            fthr = MQ && prm().qoff ? (uint32_t)win + (uint32_t)prm().filter_deltas       // bucket W + F
-                                : A::upper((uint32_t)win, prm().delta, prm().filter_deltas);  // (W + F) * delta
+            fthr = MQ && P.qoff ? (uint32_t)win + (uint32_t)P.filter_deltas       // bucket W + F
+                                : A::upper((uint32_t)win, P.delta, P.filter_deltas);  // (W + F) * delta
         }
         if (l1_lockfree()) {
             l1_write_lf<K>(e, valid, count_add, fthr);
-            if (prm().wb > 0) {
+            if (P.wb > 0) {
                 // L1V periodic flush (Section 3.4): every wb-th write moves L1 to L2
                 uint32_t wc = 0;
                 if (lane == 0) wc = atomicAdd(&S()->writes, 1u) + 1u;
                 wc = __shfl_sync(kFull, wc, 0);
-                if (wc % (uint32_t)prm().wb == 0u) {
+                if (wc % (uint32_t)P.wb == 0u) {
                     bool v = false;
                     uint2 x = make_uint2(0, 0);
-                    for (uint32_t n = 0; n <= (uint32_t)prm().l1_cap / 32u && l1_read_lf(v, x); n++)
+                    for (uint32_t n = 0; n <= (uint32_t)P.l1_cap / 32u && l1_read_lf(v, x); n++)
                         dec += l2_write(v, x);
                     stat(kStFlush, 1);
                 }
@@ -1179,14 +1151,14 @@ struct Worker {
         if (!lock()) return;
         l1_place<K>(e, valid, out, fthr, count_add);
         bool flush = false;
-        if (prm().wb > 0) {
+        if (P.wb > 0) {
             uint32_t wcount = 0;
             if (lane == 0) {
                 wcount = *(volatile uint32_t*)&S()->writes + 1u;
                 *(volatile uint32_t*)&S()->writes = wcount;
             }
             wcount = __shfl_sync(kFull, wcount, 0);
-            flush = (wcount % (uint32_t)prm().wb) == 0u;
+            flush = (wcount % (uint32_t)P.wb) == 0u;
         }
         if (flush) l1_flush_locked();
         unlock();
@@ -1202,14 +1174,14 @@ struct Worker {
         uint32_t any = 0;
         if (lane == 0) {
             any = *(volatile uint32_t*)&S()->head != *(volatile uint32_t*)&S()->tail;
-            if (prm().l1_type == 1) any |= *(volatile uint32_t*)&S()->fhead != *(volatile uint32_t*)&S()->ftail;
+            if (P.l1_type == 1) any |= *(volatile uint32_t*)&S()->fhead != *(volatile uint32_t*)&S()->ftail;
         }
         if (!__shfl_sync(kFull, any, 0)) return false;
         if (l1_lockfree()) return l1_read_lf(valid, e);
         if (!lock()) return false;
-        const uint32_t cap = (uint32_t)prm().l1_cap;
+        const uint32_t cap = (uint32_t)P.l1_cap;
         uint32_t h = sread(&S()->head), t = sread(&S()->tail);
-        if (prm().l1_type == 1 && h == t) {
+        if (P.l1_type == 1 && h == t) {
             // near vector drained: NF = min(far) + delta, then re-partition far
             const uint32_t half = cap >> 1;
             uint32_t fh = sread(&S()->fhead), ft = sread(&S()->ftail);
@@ -1218,7 +1190,7 @@ struct Worker {
                 for (uint32_t i = fh + lane; i - fh < ft - fh; i += 32)
                     mn = min(mn, vld(&L1()[half + (i & (half - 1u))]).y);
                 mn = __reduce_min_sync(kFull, mn);
-                uint32_t nf = A::plus_delta(mn, prm().delta);
+                uint32_t nf = A::plus_delta(mn, P.delta);
                 uint32_t nt = t, nft = ft;
                 uint32_t count = ft - fh;
                 for (uint32_t base = 0; base < count; base += 32) {
@@ -1248,7 +1220,7 @@ struct Worker {
         uint32_t c = t - h < 32u ? t - h : 32u;
         valid = lane < c;
         if (valid) {
-            uint32_t idx = prm().l1_type == 1 ? ((h + lane) & ((cap >> 1) - 1u)) : ((h + lane) & l1_mask());
+            uint32_t idx = P.l1_type == 1 ? ((h + lane) & ((cap >> 1) - 1u)) : ((h + lane) & l1_mask());
             e = vld(&L1()[idx]);
         }
         __syncwarp();
@@ -1263,7 +1235,7 @@ struct Worker {
         uint32_t f = 0;
         if (lane == 0) {
             uint32_t h = *(volatile uint32_t*)&S()->head, t = *(volatile uint32_t*)&S()->tail;
-            uint32_t cap = (uint32_t)prm().l1_cap >> (prm().l1_type == 1 ? 1 : 0);
+            uint32_t cap = (uint32_t)P.l1_cap >> (P.l1_type == 1 ? 1 : 0);
             uint32_t used = t - h;
             f = used < cap ? cap - used : 0u;
         }
@@ -1281,7 +1253,7 @@ struct Worker {
         const uint32_t mine = (lane >= 1u && lane < got) ? cnt : 0u;
         uint32_t incl = mine;
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
+        for (int o = 1; o < kMaxClaim; o <<= 1) {
             const uint32_t x = __shfl_up_sync(kFull, incl, o);
             if (lane >= (uint32_t)o) incl += x;
         }
@@ -1291,7 +1263,7 @@ struct Worker {
         uint32_t base = 0;
         int ok = 1;
         if (lane == 0 && rest) {
-            const uint32_t cap = (uint32_t)prm().l1_cap;
+            const uint32_t cap = (uint32_t)P.l1_cap;
             uint32_t tl = *(volatile uint32_t*)&S()->tail;
             for (;;) {
                 const uint32_t h = *(volatile uint32_t*)&S()->head;
@@ -1307,13 +1279,13 @@ struct Worker {
         }
         if (!__shfl_sync(kFull, ok, 0)) return false;
         base = __shfl_sync(kFull, base, 0);
-        const size_t slot0 = (size_t)ring * prm().l2.nch;
-        const uint32_t mask = prm().l2.nch - 1u;
+        const size_t slot0 = (size_t)ring * P.l2.nch;
+        const uint32_t mask = P.l2.nch - 1u;
         // chunk 0: this warp's batch
         {
             const uint32_t c0 = __shfl_sync(kFull, cnt, 0);
             valid = lane < c0;
-            if (valid) e = prm().l2.data[(slot0 + (t & mask)) * kChunk + lane];
+            if (valid) e = P.l2.data[(slot0 + (t & mask)) * kChunk + lane];
             count_live(valid, e.x, -1);
         }
         // chunks 1 .. got - 1 into L1, four loads in flight per lane
@@ -1326,7 +1298,7 @@ struct Worker {
                 const uint32_t j = j0 + k;
                 const uint32_t cj = __shfl_sync(kFull, cnt, j & 31u);
                 v[k] = j < got && lane < cj;
-                x[k] = v[k] ? prm().l2.data[(slot0 + ((t + j) & mask)) * kChunk + lane] : make_uint2(0u, 0u);
+                x[k] = v[k] ? P.l2.data[(slot0 + ((t + j) & mask)) * kChunk + lane] : make_uint2(0u, 0u);
             }
 #pragma unroll
             for (uint32_t k = 0; k < 4; k++) {
@@ -1338,7 +1310,7 @@ struct Worker {
                     uint32_t spins = 0;
                     while (!slot_try_put(sl, x[k])) {
                         if ((++spins & 255u) == 0 && expired()) {
-                            raise_error(prm().ctrl, kErrTimeout, 12, 0);
+                            raise_error(P.ctrl, kErrTimeout, 12, 0);
                             break;
                         }
                     }
@@ -1348,7 +1320,7 @@ struct Worker {
         __syncwarp();
         if (lane < got) {
             fence_gpu();
-            st_release(prm().l2.seq + slot0 + ((t + lane) & mask), t + lane + prm().l2.nch);
+            st_release(P.l2.seq + slot0 + ((t + lane) & mask), t + lane + P.l2.nch);
         }
         __syncwarp();
         return true;
@@ -1363,7 +1335,7 @@ struct Worker {
         valid = false;
         int role = 0;
         if (lane == 0) {
-            role = atomicAdd(&S()->refill, 1) < prm().refillers;
+            role = atomicAdd(&S()->refill, 1) < P.refillers;
             if (!role) atomicSub(&S()->refill, 1);
         }
         role = __shfl_sync(kFull, role, 0);
@@ -1376,7 +1348,7 @@ struct Worker {
 #else
         stage_flush(false);
 #endif
-        uint32_t want = (uint32_t)prm().claim;
+        uint32_t want = (uint32_t)P.claim;
         const uint32_t room = l1_free() / kChunk;
         if (want > room + 1u) want = room + 1u;
         uint32_t ring = 0, t = 0;
@@ -1453,7 +1425,7 @@ struct Worker {
             e[r] = l0[r];
         }
         l0h = l0t = 0;
-        if (prm().l2_only) {
+        if (P.l2_only) {
             // single-queue baseline: no L1, the elements go to L2
 #pragma unroll
             for (int r = 0; r < R; r++) dec += l2_write(v[r], e[r]);
@@ -1497,19 +1469,19 @@ struct Worker {
 
     // ---- far staging -------------------------------------------------------
     // Heavy-arc writes wait in a per-warp buffer.  Without block staging they
-    // go to L2 in groups of up to 32.  With block staging (prm().stage) the warps
+    // go to L2 in groups of up to 32.  With block staging (P.stage) the warps
     // of a block pool them per L2 bucket in shared memory under the staging lock,
     // and only full 32-element chunks go to L2 -- one warp's writes spread
     // over many buckets, so this is what keeps the chunks full.  Writes for
-    // the window's first prm().direct buckets (and hub slices) are urgent and go
+    // the window's first P.direct buckets (and hub slices) are urgent and go
     // to L2 at once; partial buckets are flushed when they become urgent (a
-    // refill sends those of the first prm().direct buckets) or the block runs dry.
+    // refill sends those of the first P.direct buckets) or the block runs dry.
 
     // absolute bucket of an element: floor(d / delta), shifted by the query's
     // admission offset when queries started at different times (serving)
     __device__ __forceinline__ uint32_t abs_bucket(uint32_t key, uint32_t d) const {
-        uint32_t ab = A::bucket(d, prm().delta);
-        if (MQ && prm().qoff) ab += __ldg(prm().qoff + key_query(key));
+        uint32_t ab = A::bucket(d, P.delta);
+        if (MQ && P.qoff) ab += __ldg(P.qoff + key_query(key));
         return ab;
     }
 
@@ -1519,15 +1491,15 @@ struct Worker {
     // up to kWindowGuard buckets no ring holds elements of two buckets of the
     // window.  Elements below W keep their bucket (the writer pulls W back).
     __device__ __forceinline__ uint32_t clamp_bucket(uint32_t ab, uint32_t W) const {
-        const uint32_t reach = (uint32_t)prm().bmax > 2u * kWindowGuard ? (uint32_t)prm().bmax - kWindowGuard
-                                                                  : (uint32_t)prm().bmax;
+        const uint32_t reach = (uint32_t)P.bmax > 2u * kWindowGuard ? (uint32_t)P.bmax - kWindowGuard
+                                                                  : (uint32_t)P.bmax;
         if (ab > W && ab - W >= reach) return W + reach - 1u;
         return ab;
     }
 
     __device__ __forceinline__ uint32_t ring_bucket(uint32_t key, uint32_t d, uint32_t W, uint32_t& ab) const {
         ab = clamp_bucket(abs_bucket(key, d), W);
-        return ab % (uint32_t)prm().bmax;
+        return ab % (uint32_t)P.bmax;
     }
 
     // ---- lock-free block staging (SSSP_LF_STAGE) ----------------------------
@@ -1549,7 +1521,7 @@ struct Worker {
             uint32_t spins = 0;
             while (!slot_try_take(sl, y)) {
                 if ((++spins & 255u) == 0 && expired()) {
-                    raise_error(prm().ctrl, kErrTimeout, 13, (int)b);
+                    raise_error(P.ctrl, kErrTimeout, 13, (int)b);
                     break;
                 }
             }
@@ -1581,81 +1553,18 @@ struct Worker {
     }
 
     // Places the lanes' staged elements sv (bucket b each) in their buckets'
-    // rings; elements that do not fit go to L2 at once.  A bucket that now
-    // holds a full chunk is shipped to L2.  One bucket ring at a time: every
-    // reservation is filled, and every chunk taken is read and cleared,
-    // before the warp touches another ring.  Within one ring no wait can
-    // close a cycle (a taker waits only for slots at most 31 ahead of what
-    // it holds, a writer only for slots at least 33 behind what it reserved,
-    // with kStageCap = 64 and at most 32 per reservation); a warp waiting in
-    // one ring while holding slots of another could (the lanes re-converge
-    // after each wait loop).
-    __device__ void stage_place_lf(bool sv, uint2 x, uint32_t b) {
-        bool over = false;
-        uint32_t todo = __ballot_sync(kFull, sv);
-        while (todo) {
-            const uint32_t bg = __shfl_sync(kFull, b, __ffs(todo) - 1);
-            const bool in = sv && b == bg;
-            const uint32_t grp = __ballot_sync(kFull, in);
-            todo &= ~grp;
-            uint32_t base = 0, take = 0;
-            if (lane == 0) {
-                const uint32_t k = (uint32_t)__popc(grp);
-                uint32_t t = *(volatile uint32_t*)&S()->scnt[bg];
-                for (;;) {
-                    const uint32_t h = *(volatile uint32_t*)&S()->shead[bg];
-                    const uint32_t used = t - h;
-                    take = used < (uint32_t)kStageCap ? min(k, (uint32_t)kStageCap - used) : 0u;
-                    if (take == 0) break;
-                    const uint32_t old = atomicCAS(&S()->scnt[bg], t, t + take);
-                    if (old == t) break;
-                    t = old;
-                }
-                base = t;
-            }
-            base = __shfl_sync(kFull, base, 0);
-            take = __shfl_sync(kFull, take, 0);
-            const uint32_t rank = __popc(grp & lanemask_lt());
-            const bool placed = in && rank < take;
-            over = over || (in && !placed);
-            if (placed) {
-                volatile uint2* sl = stg_slot(bg, base + rank);
-                uint32_t spins = 0;
-                while (!slot_try_put(sl, x)) {
-                    if ((++spins & 255u) == 0 && expired()) {
-                        raise_error(prm().ctrl, kErrTimeout, 14, (int)bg);
-                        break;
-                    }
-                }
-            }
-            __syncwarp();
-            // a full chunk of this bucket goes to L2
-            uint32_t h = 0;
-            int own = 0;
-            if (lane == 0) {
-                h = *(volatile uint32_t*)&S()->shead[bg];
-                const uint32_t t = *(volatile uint32_t*)&S()->scnt[bg];
-                own = t - h >= 32u && atomicCAS(&S()->shead[bg], h, h + 32u) == h;
-            }
-            if (__shfl_sync(kFull, own, 0)) {
-                h = __shfl_sync(kFull, h, 0);
-                bool vy = false;
-                uint2 y = make_uint2(0, 0);
-                stage_read(bg, h, 32u, vy, y);
-                dec += l2_write(vy, y);
-            }
-        }
-        dec += l2_write(over, x);
-    }
-
-#if SSSP_STAGE_PAR
-    // stage_place_lf with every bucket group placed at once: the group leaders
-    // reserve their slots concurrently, every lane then deposits its element
-    // (each lane waits only for its own slot), and only after all deposits
-    // are full chunks taken, one ring at a time.  A lane never holds a
-    // reservation while waiting as a taker, and no lane's deposit is ordered
-    // after another lane's wait.
-    __device__ void stage_place_par(bool sv, uint2 x, uint32_t b) {
+    // rings; elements that do not fit go to L2 at once.  The leaders of the
+    // bucket groups reserve their slots concurrently (a CAS on the ring's
+    // tail, bounded by head + kStageCap), every lane then deposits its
+    // element in its mailbox slot, and only after all deposits are the full
+    // chunks taken and shipped to L2, one ring at a time.  No wait can close
+    // a cycle: a writer lane waits only for its own slot to be emptied by the
+    // taker of the previous lap (at least 33 slots behind its reservation), a
+    // taker only for deposits into the slots it took (at most 31 ahead, with
+    // kStageCap = 64 and at most 32 per take); no lane's deposit is ordered
+    // after another lane's wait, and a warp takes chunks only while it holds
+    // no reservation, so no wait depends on a second ring.
+    __device__ void stage_place(bool sv, uint2 x, uint32_t b) {
         const uint32_t grp = __match_any_sync(kFull, sv ? b : 0xffffffffu);
         const uint32_t rank = __popc(grp & lanemask_lt());
         const bool leader = sv && rank == 0u;
@@ -1684,7 +1593,7 @@ struct Worker {
             uint32_t spins = 0;
             while (!slot_try_put(sl, x)) {
                 if ((++spins & 255u) == 0 && expired()) {
-                    raise_error(prm().ctrl, kErrTimeout, 14, (int)b);
+                    raise_error(P.ctrl, kErrTimeout, 14, (int)b);
                     break;
                 }
             }
@@ -1718,7 +1627,6 @@ struct Worker {
         }
         dec += l2_write(over, x);
     }
-#endif
 
     // Takes up to 32 staged elements of bucket ring index b (lock held).
     __device__ uint32_t stage_take(uint32_t b, bool& v, uint2& x) {
@@ -1733,9 +1641,9 @@ struct Worker {
     }
 
     // Moves staged elements to L2: all buckets (all = true, the block ran
-    // dry) or only those of the window's first prm().direct buckets.
+    // dry) or only those of the window's first P.direct buckets.
     __device__ SSSP_NOINLINE void stage_flush(bool all) {
-        if (!prm().stage) return;
+        if (!P.stage) return;
         unsigned long long win = 0;
         if (lane == 0) win = window();
         const uint32_t W = (uint32_t)__shfl_sync(kFull, win, 0);
@@ -1743,8 +1651,8 @@ struct Worker {
             // unlocked look for a non-empty candidate bucket
             uint32_t cnt = 0;
             const uint32_t b = lane;
-            const bool cand = b < (uint32_t)prm().bmax &&
-                              (all || ((b + (uint32_t)prm().bmax - W % (uint32_t)prm().bmax) % (uint32_t)prm().bmax) < prm().direct);
+            const bool cand = b < (uint32_t)P.bmax &&
+                              (all || ((b + (uint32_t)P.bmax - W % (uint32_t)P.bmax) % (uint32_t)P.bmax) < P.direct);
             if (cand) {
                 cnt = *(volatile uint32_t*)&S()->scnt[b];
                 if (SSSP_LF_STAGE) cnt -= *(volatile uint32_t*)&S()->shead[b];
@@ -1768,7 +1676,7 @@ struct Worker {
     __device__ SSSP_NOINLINE void far_flush(uint32_t upto) {
         if (nfar <= upto) return;
         unsigned long long win = 0;
-        if (prm().stage && lane == 0) win = window();
+        if (P.stage && lane == 0) win = window();
         const uint32_t W = (uint32_t)__shfl_sync(kFull, win, 0);
         while (nfar > upto) {
             const uint32_t take = nfar - upto < 32u ? nfar - upto : 32u;
@@ -1777,13 +1685,13 @@ struct Worker {
             if (v) x = farbuf()[nfar - take + lane];
             __syncwarp();
             nfar -= take;
-            if (!prm().stage) {
+            if (!P.stage) {
                 dec += l2_write(v, x);
                 continue;
             }
             uint32_t ab = 0;
             const uint32_t b = v ? ring_bucket(x.x, x.y, W, ab) : 0u;
-            const bool urgent = v && (ab < W + prm().direct || key_vertex(x.x) >= (uint32_t)prm().n);
+            const bool urgent = v && (ab < W + P.direct || key_vertex(x.x) >= (uint32_t)P.n);
             dec += l2_write(urgent, x);
             const bool sv = v && !urgent;
             if (!__any_sync(kFull, sv)) continue;
@@ -1793,11 +1701,7 @@ struct Worker {
             if (lane == 0 && unc != 0) atomicAdd(&S()->acct, ((unsigned long long)(uint32_t)unc) << 32);
             unc = 0;
             __syncwarp();
-#if SSSP_STAGE_PAR
-            stage_place_par(sv, x, b);
-#else
-            stage_place_lf(sv, x, b);
-#endif
+            stage_place(sv, x, b);
             continue;
 #endif
             bool vy = false, over = false;
@@ -1926,19 +1830,19 @@ struct Worker {
     __device__ __forceinline__ void push_round(bool imp, uint32_t key, uint32_t nd, uint32_t w, uint32_t front,
                                                uint32_t& n_imp, uint32_t& n_mark) {
         n_imp += (uint32_t)__popc(__ballot_sync(kFull, imp));
-        if (prm().pend) {
+        if (P.pend) {
             // an improved vertex already queued at an earlier-or-equal bucket
             // is not queued again: its queued element is relaxed with the
             // distance current when it is read
             bool q = false;
             if (imp) {
                 const uint32_t b = abs_bucket(key, nd);
-                q = atom_min_release(prm().pend + dist_index(key), b) > b;
+                q = atom_min_release(P.pend + dist_index(key), b) > b;
             }
             n_mark += (uint32_t)__popc(__ballot_sync(kFull, imp && !q));
             imp = q;
         }
-        if (prm().dedup) {
+        if (P.dedup) {
             // in-warp duplicates (Listing 1's write of a warp's improved
             // vertices): lanes whose arcs improved the same target this round
             // are matched; one write per target is enough, the one with the
@@ -1957,8 +1861,8 @@ struct Worker {
         }
         // a shadow vertex (a slice of a hub's arcs) always goes to L2 so that
         // the slices of one hub spread over all blocks
-        const bool inside = MQ && prm().qoff ? abs_bucket(key, nd) <= front : nd <= front;
-        const bool nearv = imp && !prm().l2_only && w <= prm().near_w && inside && key_vertex(key) < (uint32_t)prm().n;
+        const bool inside = MQ && P.qoff ? abs_bucket(key, nd) <= front : nd <= front;
+        const bool nearv = imp && !P.l2_only && w <= P.near_w && inside && key_vertex(key) < (uint32_t)P.n;
         const uint32_t m = __ballot_sync(kFull, nearv);
         if (m) {
             if (nearv) scratch()[__popc(m & lanemask_lt())] = make_uint2(key, nd);
@@ -1994,8 +1898,8 @@ struct Worker {
         r.q = MQ ? __shfl_sync(kFull, myq, j) : 0u;
         r.pu = PRED != 0 ? __shfl_sync(kFull, pu, j) : 0u;
         r.in = g < total;
-        r.a = r.in ? ld_arc(prm().adj + (ors + (g - oex))) : make_uint2(0u, 0u);
-        if (prm().unit_w) r.a.y = r.a.x >= (uint32_t)prm().n ? 0u : 1u;
+        r.a = r.in ? ld_arc(P.adj + (ors + (g - oex))) : make_uint2(0u, 0u);
+        if (P.unit_w) r.a.y = r.a.x >= (uint32_t)P.n ? 0u : 1u;
         return r;
     }
 
@@ -2013,18 +1917,18 @@ struct Worker {
         uint32_t key = el.x, du = el.y;
         int32_t rs = 0, deg = 0;
         bool stale = false;
-        if (valid && (key_vertex(key) >= (uint32_t)prm().nv || key_query(key) >= (uint32_t)prm().nq)) {
-            raise_error(prm().ctrl, kErrElement, 8, (int)key);
+        if (valid && (key_vertex(key) >= (uint32_t)P.nv || key_query(key) >= (uint32_t)P.nq)) {
+            raise_error(P.ctrl, kErrElement, 8, (int)key);
             valid = false;
         }
-        if (valid && prm().pend) {
+        if (valid && P.pend) {
             // pending marks: the read takes the vertex's mark; a mark already
             // taken by an earlier read means no improvement since that read's
             // relaxation, so the element is stale.  Otherwise the arcs are
             // relaxed from the current distance (never above the element's).
             const uint32_t v = key_vertex(key);
-            const int32_t r0 = ld_row(prm().row_ptr + v), r1 = ld_row(prm().row_ptr + v + 1);
-            const uint32_t mark = atom_exch_acquire(prm().pend + dist_index(key), kInfU32);
+            const int32_t r0 = ld_row(P.row_ptr + v), r1 = ld_row(P.row_ptr + v + 1);
+            const uint32_t mark = atom_exch_acquire(P.pend + dist_index(key), kInfU32);
             if (mark == kInfU32) {
                 valid = false;
                 stale = true;
@@ -2040,7 +1944,7 @@ struct Worker {
             // round trip instead of two); a stale vertex ignores them
             const uint32_t v = key_vertex(key);
             const uint32_t cur = dpart(ld_dist(dist() + dist_index(key)));
-            const int32_t r0 = ld_row(prm().row_ptr + v), r1 = ld_row(prm().row_ptr + v + 1);
+            const int32_t r0 = ld_row(P.row_ptr + v), r1 = ld_row(P.row_ptr + v + 1);
             if (du > cur) {
                 valid = false;
                 stale = true;
@@ -2055,17 +1959,17 @@ struct Worker {
                 stale = true;
             } else {
                 uint32_t v = key_vertex(key);
-                rs = ld_row(prm().row_ptr + v);
-                deg = ld_row(prm().row_ptr + v + 1) - rs;
+                rs = ld_row(P.row_ptr + v);
+                deg = ld_row(P.row_ptr + v + 1) - rs;
 #if SSSP_SHADOW_OWNER
-                if (v >= (uint32_t)prm().n) {
+                if (v >= (uint32_t)P.n) {
                     // a hub slice: when the hub has improved since the slice was
                     // queued, relax from the hub's current distance and give the
                     // slice that distance, so the hub's next relaxation of its
                     // zero-weight links finds nothing to improve and queues no
                     // second copy of the slice
-                    const uint32_t ow = (uint32_t)__ldg(prm().owner + (v - (uint32_t)prm().n));
-                    const size_t oidx = MQ ? (size_t)key_query(key) * (size_t)prm().nv + ow : (size_t)ow;
+                    const uint32_t ow = (uint32_t)__ldg(P.owner + (v - (uint32_t)P.n));
+                    const size_t oidx = MQ ? (size_t)key_query(key) * (size_t)P.nv + ow : (size_t)ow;
                     const uint32_t dO = dpart(ld_dist(dist() + oidx));
                     if (dO < du) {
                         du = dO;
@@ -2092,11 +1996,11 @@ struct Worker {
         }
         int32_t ex = incl - deg;
         // defer vertices starting beyond max_arcs (never the first one)
-        const bool defer = valid && ex >= prm().max_arcs;
+        const bool defer = valid && ex >= P.max_arcs;
         const uint32_t dm = __ballot_sync(kFull, defer);
         if (dm) {
             // a deferred vertex is queued again (in L0): it gets its mark back
-            if (defer && prm().pend) atomicMin(prm().pend + dist_index(key), abs_bucket(key, el.y));
+            if (defer && P.pend) atomicMin(P.pend + dist_index(key), abs_bucket(key, el.y));
             if (defer) scratch()[__popc(dm & lanemask_lt())] = el;
             __syncwarp();
             l0_push(__popc(dm), true);
@@ -2119,24 +2023,24 @@ struct Worker {
         // the window front for this batch (see push_round); no bound when
         // every write is local (near_deltas = 0, as in Listing 1)
         uint32_t front = kInfU32;
-        if (SSSP_FRONT_BOUND && prm().near_w != kInfU32) {
+        if (SSSP_FRONT_BOUND && P.near_w != kInfU32) {
             unsigned long long win = 0;
             if (lane == 0) win = window();
             const uint32_t W = (uint32_t)__shfl_sync(kFull, win, 0);
-            front = MQ && prm().qoff ? W + (uint32_t)prm().filter_deltas : A::upper(W, prm().delta, prm().filter_deltas);
+            front = MQ && P.qoff ? W + (uint32_t)P.filter_deltas : A::upper(W, P.delta, P.filter_deltas);
         }
         // predecessor id: a shadow vertex stands for its owner
         uint32_t pu = 0;
         if (PRED != 0 && valid) {
             uint32_t v = key_vertex(key);
-            pu = v < (uint32_t)prm().n ? v : (uint32_t)__ldg(prm().owner + (v - (uint32_t)prm().n));
+            pu = v < (uint32_t)P.n ? v : (uint32_t)__ldg(P.owner + (v - (uint32_t)P.n));
         }
         stat(kStRelax, (unsigned long long)((uint32_t)total));
 #if SSSP_FINE_CYCLES
         stat(kCyBatch, (unsigned long long)(clock64() - cb0));
 #endif
         {
-            const int32_t sh = valid && key_vertex(key) >= (uint32_t)prm().n ? deg : 0;
+            const int32_t sh = valid && key_vertex(key) >= (uint32_t)P.n ? deg : 0;
             const int32_t shs = __reduce_add_sync(kFull, (uint32_t)sh);
             if (shs) stat(kStRelaxShadow, (unsigned long long)shs);
         }
@@ -2148,7 +2052,7 @@ struct Worker {
         for (int32_t g0 = 0; g0 < total; g0 += 32) {
             if (g0 && (g0 & 4095) == 0) {
                 int stop = 0;
-                if (lane == 0) stop = expired() || ld_volatile_int(&prm().ctrl->error) != 0;
+                if (lane == 0) stop = expired() || ld_volatile_int(&P.ctrl->error) != 0;
                 if (__shfl_sync(kFull, stop, 0)) break;
             }
 #if SSSP_FINE_CYCLES
@@ -2163,14 +2067,14 @@ struct Worker {
             uint32_t nd = 0;
             bool imp = false;
             if (cu.in) {
-                const size_t vidx = MQ ? (size_t)cu.q * (size_t)prm().nv + cu.a.x : (size_t)cu.a.x;
+                const size_t vidx = MQ ? (size_t)cu.q * (size_t)P.nv + cu.a.x : (size_t)cu.a.x;
                 imp = relax_cur(vidx, cu.pu, cu.du, cu.a.y, ld_dist(dist() + vidx), nd);
             }
 #if SSSP_FINE_CYCLES
             const long long cr1 = clock64();
             stat(kCyRound, (unsigned long long)__shfl_sync(kFull, (unsigned long long)(cr1 - cr0), 0));
 #endif
-            push_round(imp, MQ ? ((cu.q << prm().vbits) | cu.a.x) : cu.a.x, nd, cu.a.y, front, n_imp, n_mark);
+            push_round(imp, MQ ? ((cu.q << P.vbits) | cu.a.x) : cu.a.x, nd, cu.a.y, front, n_imp, n_mark);
             n_rounds++;
 #if SSSP_FINE_CYCLES
             stat(kCyPush, (unsigned long long)(clock64() - cr1));
@@ -2185,7 +2089,7 @@ struct Worker {
     __device__ __noinline__ void publish_stats() {
         if (lane == 0) {
             for (int i = 0; i < kStCount; i++)
-                if (sst()[i]) atomicAdd(&prm().ctrl->stats[i], sst()[i]);
+                if (sst()[i]) atomicAdd(&P.ctrl->stats[i], sst()[i]);
         }
     }
 
@@ -2193,14 +2097,14 @@ struct Worker {
     __device__ __noinline__ void sample() {
         const unsigned long long now = gtime();
         BlockShared* B = S();
-        if (now < B->next_sample || B->nsamples >= (uint32_t)prm().timeline_cap) return;
-        B->next_sample = now + prm().timeline_ns;
-        unsigned long long* o = prm().timeline + (size_t)B->nsamples * kTimelineFields;
+        if (now < B->next_sample || B->nsamples >= (uint32_t)P.timeline_cap) return;
+        B->next_sample = now + P.timeline_ns;
+        unsigned long long* o = P.timeline + (size_t)B->nsamples * kTimelineFields;
         o[0] = now - B->t0;
-        o[2] = ld_acquire64(&prm().ctrl->done);      // done before reserve: done <= reserve
-        o[1] = ld_acquire64(&prm().ctrl->reserve);
-        o[3] = ld_acquire64(&prm().ctrl->processed);
-        o[4] = ld_acquire64(&prm().ctrl->window);
+        o[2] = ld_acquire64(&P.ctrl->done);      // done before reserve: done <= reserve
+        o[1] = ld_acquire64(&P.ctrl->reserve);
+        o[3] = ld_acquire64(&P.ctrl->processed);
+        o[4] = ld_acquire64(&P.ctrl->window);
         o[5] = *(volatile uint32_t*)&B->busy;
         B->nsamples++;
     }
@@ -2212,13 +2116,13 @@ struct Worker {
         for (;;) {
             mark(1, iter);
             stat(kStIter, 1);
-            if (prm().timeline && blockIdx.x == 0 && threadIdx.x == 0) sample();
-            if ((++iter & 7u) == 0 || idle_ns || prm().slice_ns) {
+            if (P.timeline && blockIdx.x == 0 && threadIdx.x == 0) sample();
+            if ((++iter & 7u) == 0 || idle_ns || P.slice_ns) {
                 int stop = 0;
                 if (lane == 0) {
                     stop = aborted();
                     if (!stop && expired()) {
-                        raise_error(prm().ctrl, kErrTimeout, 7, 0);
+                        raise_error(P.ctrl, kErrTimeout, 7, 0);
                         stop = 1;
                     }
                     if (!stop && gtime() > S()->slice_end) stop = 2;  // end of a serving slice
@@ -2258,10 +2162,10 @@ struct Worker {
                 int fin = 0;
                 if (rf == 0 && lane == 0) {
                     // L2 looked empty to this block's refiller: test termination
-                    unsigned long long d = ld_acquire64(&prm().ctrl->done);
-                    unsigned long long r = ld_acquire64(&prm().ctrl->reserve);
+                    unsigned long long d = ld_acquire64(&P.ctrl->done);
+                    unsigned long long r = ld_acquire64(&P.ctrl->reserve);
                     if (d == r) {
-                        atomicExch(&prm().ctrl->finished, 1);
+                        atomicExch(&P.ctrl->finished, 1);
                         fin = 1;
                     }
                 }
@@ -2275,14 +2179,14 @@ struct Worker {
             }
             idle_ns = 0;
             mark(7, iter);
-            if (prm().timeline) {
+            if (P.timeline) {
                 // run-time sampling only: the batch's elements, and block 0's busy warps
                 const uint32_t nb = (uint32_t)__popc(__ballot_sync(kFull, valid));
-                if (lane == 0) atomicAdd(&prm().ctrl->processed, (unsigned long long)nb);
+                if (lane == 0) atomicAdd(&P.ctrl->processed, (unsigned long long)nb);
                 if (blockIdx.x == 0 && lane == 0) atomicAdd(&S()->busy, 1u);
             }
             dec += relax_batch(valid, e);
-            if (prm().timeline && blockIdx.x == 0 && lane == 0) atomicSub(&S()->busy, 1u);
+            if (P.timeline && blockIdx.x == 0 && lane == 0) atomicSub(&S()->busy, 1u);
             stat(kCyRelax, (unsigned long long)((unsigned long long)(clock64() - c3)));
             mark(10, iter);
             acct_apply();
@@ -2297,7 +2201,7 @@ struct Worker {
     // no-op; at the end of a serving slice the work continues from L2 in the
     // next launch.
     __device__ __noinline__ void drain_warp() {
-        if (ld_volatile_int(&prm().ctrl->error) != 0) return;
+        if (ld_volatile_int(&P.ctrl->error) != 0) return;
         const uint32_t len = l0t - l0h;
         if (len) {
 #pragma unroll
@@ -2315,14 +2219,14 @@ struct Worker {
     // End of a launch, one warp per block after every warp drained: move L1
     // and the block staging to L2, then publish the block's count.
     __device__ __noinline__ void drain_block() {
-        if (ld_volatile_int(&prm().ctrl->error) != 0) return;
+        if (ld_volatile_int(&P.ctrl->error) != 0) return;
         if (l1_lockfree()) {
             bool v = false;
             uint2 x = make_uint2(0, 0);
             while (l1_read_lf(v, x)) dec += l2_write(v, x);
         } else if (lock()) {
-            if (prm().l1_type == 1) {
-                const uint32_t half = (uint32_t)prm().l1_cap >> 1;
+            if (P.l1_type == 1) {
+                const uint32_t half = (uint32_t)P.l1_cap >> 1;
                 for (int rg = 0; rg < 2; rg++) {
                     uint32_t* hp = rg ? &S()->fhead : &S()->head;
                     uint32_t* tp = rg ? &S()->ftail : &S()->tail;
@@ -2359,7 +2263,7 @@ struct Worker {
             // nothing may stay behind in the block: its count must be zero,
             // and the L2 reads it finished are published to ctrl.done
             const unsigned long long v = *(volatile unsigned long long*)&S()->acct;
-            if ((uint32_t)(v >> 32) != 0u) raise_error(prm().ctrl, kErrState, 9, (int)(v >> 32));
+            if ((uint32_t)(v >> 32) != 0u) raise_error(P.ctrl, kErrState, 9, (int)(v >> 32));
             else try_flush();
         }
         __syncwarp();
@@ -2367,11 +2271,12 @@ struct Worker {
 };
 
 template <int WT, int PRED, bool MQ, int R>
-#if SSSP_GRID_CONST
+// The parameters are a grid constant (no local copy is made when their
+// address is taken); the prologue copies them to shared memory, from where
+// the workers read them: with a local copy every field read was a
+// local-memory load, and through the grid constant the out-of-line queue
+// functions read them with generic loads.
 __global__ void __launch_bounds__(1024, 1) mlmq_kernel(const __grid_constant__ KParams P) {
-#else
-__global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
-#endif
     BlockShared* S = reinterpret_cast<BlockShared*>(mlmq_smem);
     volatile uint2* l1 = reinterpret_cast<volatile uint2*>(mlmq_smem + P.l1_off);
     if (threadIdx.x == 0) {
@@ -2402,7 +2307,6 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
         volatile uint2* st = reinterpret_cast<volatile uint2*>(mlmq_smem + P.stage_off);
         for (int i = threadIdx.x; i < P.bmax * kStageCap; i += blockDim.x) vst(st + i, make_uint2(kEmptyKey, 0u));
     }
-#if SSSP_PARAM_SMEM
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(&P);
         uint32_t* dst = reinterpret_cast<uint32_t*>(&S->params);
@@ -2410,10 +2314,6 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(KParams P) {
     }
     __syncthreads();
     Worker<WT, PRED, MQ, R> w(S->params);
-#else
-    __syncthreads();
-    Worker<WT, PRED, MQ, R> w(P);
-#endif
     w.run();
     if (P.slice_ns) {
         // serving slice: every warp has drained its private state; one warp

@@ -60,6 +60,9 @@ sssp_config prior_config(const Graph* g) {
             // 6.2 ms against 6.7 ms with the first two buckets written directly, and the
             // 256-query batch on R-MAT-20 289 ms against 297 ms
             c.direct_buckets = 0;
+            // 16 rings per bucket: fewer refills contend for one ring's read ticket
+            // (R-MAT-22 on GB300: 4.70 ms against 4.93 with 8; 32: 5.31 ms)
+            c.shards = 16;
             break;
         case kMesh:
             c.l1_type = SSSP_L1_FILTER;
@@ -204,8 +207,9 @@ extern "C" int sssp_autotune(sssp_graph* gh, const int32_t* srcs, int32_t nsrc, 
             c.shards = sh;
             cands.push_back(c);
         }
-        for (int cl : {1, 8}) {
+        for (int cl : {4, 8, 16}) {
             sssp_config c = best;
+            if (c.claim == cl) continue;
             c.claim = cl;
             cands.push_back(c);
         }
@@ -331,7 +335,7 @@ extern "C" int sssp_autotune_batch(sssp_graph* gh, const int32_t* srcs, int32_t 
                 c.l1_cap = l1;
                 cands.push_back(c);
             }
-            for (int cl : {2, 4, 8}) {
+            for (int cl : {4, 8, 16}) {
                 sssp_config c = best;
                 c.claim = cl;
                 cands.push_back(c);
