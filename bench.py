@@ -60,7 +60,7 @@ def _strip_comments(src: str) -> str:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("mlmq.cuh", "kernels_u32.cu"):
+    for f in ("mlmq.cuh", "kernels_inst.cuh", "kernels_u32.cu"):
         text = open(os.path.join(ROOT, "paper_2602_10080_gb300", "csrc", f), encoding="utf-8").read()
         h.update(_strip_comments(text).encode())
     return h.hexdigest()[:16]

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "libsssp.so")
 OBJ = os.path.join(HERE, "_build")
 
-SOURCES = ["kernels_u32.cu", "kernels_f32.cu", "sssp_api.cu", "sssp_autotune.cu", "sssp_serve.cu",
-           "sssp_noalloc.cu"]
+SOURCES = ["kernels_u32.cu", "kernels_u32x.cu", "kernels_f32.cu", "kernels_f32x.cu", "sssp_api.cu",
+           "sssp_autotune.cu", "sssp_serve.cu", "sssp_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include")]

@@ -209,6 +209,11 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
     uint32_t v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -290,6 +295,17 @@ __device__ __forceinline__ bool ahead(uint32_t w, uint32_t r) { return (int32_t)
 #ifndef SSSP_PIPELINE
 #define SSSP_PIPELINE 0
 #endif
+// Publication of a chunk (its sequence number) and of a warp's element count
+// (the block account) rely on release semantics alone: st.release.gpu orders
+// the warp's chunk stores and loads before the sequence number (the other
+// lanes' accesses through the __syncwarp before it), and the account update is
+// an atom.release.cta that the block's flusher observes before its own fence
+// and its add to ctrl.done.  SSSP_PUB_FENCE=1 adds a full fence before each
+// (on GB300: R-MAT-22 single source 1%, 256-query batch 2%, road 4096^2 5%
+// slower).
+#ifndef SSSP_PUB_FENCE
+#define SSSP_PUB_FENCE 0
+#endif
 #ifndef SSSP_NOINLINE
 #define SSSP_NOINLINE __noinline__
 #endif
@@ -349,6 +365,13 @@ __device__ __forceinline__ unsigned long long ld_dist(const unsigned long long* 
 // Pending-mark atomics: an improvement lowers the mark with release order
 // (its distance write is visible to whoever takes the mark later); a read
 // takes the mark with acquire order and only then loads the distance.
+// Adds v to a shared-memory word with release semantics at CTA scope.
+__device__ __forceinline__ unsigned long long atom_add_release_cta(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("atom.release.cta.shared::cta.add.u64 %0, [%1], %2;" : "=l"(old) : "r"(a), "l"(v) : "memory");
+    return old;
+}
 __device__ __forceinline__ uint32_t atom_min_release(uint32_t* p, uint32_t v) {
     uint32_t old;
     asm volatile("atom.release.gpu.global.min.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
@@ -438,6 +461,7 @@ struct BlockShared {
     unsigned long long t0;        // launch start (globaltimer), for run-time sampling
     unsigned long long next_sample;
     uint32_t nsamples;
+    uint32_t wcache;              // the window base as last read from ctrl.window by a warp of the block
     uint32_t busy;                // warps of the block holding a batch (sampling only)
     KParams params;               // the launch parameters, read by the workers from here
 };
@@ -478,7 +502,7 @@ __device__ __forceinline__ void fence_gpu() {
 // relaxation round and the L0/L1 paths stay inline.
 extern __shared__ __align__(16) unsigned char mlmq_smem[];
 
-template <int WT, int PRED, bool MQ, int R>
+template <int WT, int PRED, bool MQ, int R, bool X>
 struct Worker {
     // PRED: 0 = distances only (uint32 words), 1 = (dist, pred) words with the
     // smallest-index tight predecessor, 2 = (dist, pred) words set only on a
@@ -542,7 +566,7 @@ struct Worker {
 
     // debug trace of where each lane is (no-op unless P.trace is set)
     __device__ __forceinline__ void mark(uint32_t code, uint32_t iter = 0) const {
-        if (P.trace) {
+        if (X && P.trace) {
             const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
             *(volatile unsigned long long*)(P.trace + gt) =
                 ((unsigned long long)code << 48) | (unsigned long long)(iter & 0xffffffffffffull);
@@ -589,9 +613,13 @@ struct Worker {
         unc = 0;
         dec = 0;
         if (lane == 0 && delta != 0) {
-            fence_gpu();
             unsigned long long add = ((unsigned long long)(uint32_t)delta) << 32;
+#if SSSP_PUB_FENCE
+            fence_gpu();
             unsigned long long old = atomicAdd(&S()->acct, add);
+#else
+            unsigned long long old = atom_add_release_cta(&S()->acct, add);
+#endif
             if ((uint32_t)(old >> 32) + (uint32_t)delta == 0u) try_flush();
         }
         __syncwarp();
@@ -642,9 +670,18 @@ struct Worker {
     __device__ __forceinline__ void sunlock() { unlock(&S()->slock); }
 
     // ---- L2: sharded bucket rings -----------------------------------------
+    // The window base.  No data is published through it (it only steers
+    // where elements are written and read), so the load is relaxed and later
+    // loads need not wait for it.  window() reads ctrl.window and refreshes
+    // the block's copy; window_hint() returns the copy, for decisions that
+    // only group or route elements (the staging bucket, the local front, the
+    // L1 filter), where a slightly stale base costs nothing.
     __device__ __forceinline__ unsigned long long window() const {
-        return ld_acquire64(&P.ctrl->window);
+        const unsigned long long w = ld_relaxed64(&P.ctrl->window);
+        S()->wcache = (uint32_t)w;
+        return w;
     }
+    __device__ __forceinline__ uint32_t window_hint() const { return *(volatile uint32_t*)&S()->wcache; }
     __device__ __forceinline__ uint32_t home_shard() const {
         return (blockIdx.x + (threadIdx.x >> 5)) & (uint32_t)(P.shards - 1);
     }
@@ -753,7 +790,7 @@ struct Worker {
         __syncwarp();
         if (leader) {
             P.l2.cnt[slot] = (uint32_t)__popc(grp);
-            fence_gpu();
+            if (SSSP_PUB_FENCE) fence_gpu();
             st_release(P.l2.seq + slot, t + 1u);
         }
         stat(kStChunks, (unsigned long long)__popc(__ballot_sync(kFull, leader)));
@@ -800,7 +837,10 @@ struct Worker {
             const int first = __ffs(nonempty) - 1;
             const uint32_t first_rel = r0 + (uint32_t)first / S_;
             if (first_rel > 0 && lane == 0)
-                if (atomicCAS(&P.ctrl->window, win, (unsigned long long)(W + first_rel)) == win) sst()[kStAdvance]++;
+                if (atomicCAS(&P.ctrl->window, win, (unsigned long long)(W + first_rel)) == win) {
+                    sst()[kStAdvance]++;
+                    S()->wcache = W + first_rel;
+                }
             // candidates: non-empty rings of buckets within bnum of the first
             // one; hub rings only within hub_bnum of it (a hub slice is
             // relaxed once its distance is near the front, so it is rarely
@@ -869,7 +909,7 @@ struct Worker {
         count_live(valid, e.x, -1);
         __syncwarp();
         if (lane == 0) {
-            fence_gpu();
+            if (SSSP_PUB_FENCE) fence_gpu();
             st_release(P.l2.seq + slot, tj + P.l2.nch);
         }
         __syncwarp();
@@ -1123,11 +1163,9 @@ struct Worker {
         const long long c0 = clock64();
         uint32_t fthr = kInfU32;
         if (P.l1_type == 2 && filter) {
-            unsigned long long win = 0;
-            if (lane == 0) win = window();
-            win = __shfl_sync(kFull, win, 0);
-            fthr = MQ && P.qoff ? (uint32_t)win + (uint32_t)P.filter_deltas       // bucket W + F
-                                : A::upper((uint32_t)win, P.delta, P.filter_deltas);  // (W + F) * delta
+            const uint32_t win = window_hint();
+            fthr = MQ && P.qoff ? win + (uint32_t)P.filter_deltas       // bucket W + F
+                                : A::upper(win, P.delta, P.filter_deltas);  // (W + F) * delta
         }
         if (l1_lockfree()) {
             l1_write_lf<K>(e, valid, count_add, fthr);
@@ -1319,7 +1357,7 @@ struct Worker {
         }
         __syncwarp();
         if (lane < got) {
-            fence_gpu();
+            if (SSSP_PUB_FENCE) fence_gpu();
             st_release(P.l2.seq + slot0 + ((t + lane) & mask), t + lane + P.l2.nch);
         }
         __syncwarp();
@@ -1425,7 +1463,7 @@ struct Worker {
             e[r] = l0[r];
         }
         l0h = l0t = 0;
-        if (P.l2_only) {
+        if (X && P.l2_only) {
             // single-queue baseline: no L1, the elements go to L2
 #pragma unroll
             for (int r = 0; r < R; r++) dec += l2_write(v[r], e[r]);
@@ -1643,10 +1681,8 @@ struct Worker {
     // Moves staged elements to L2: all buckets (all = true, the block ran
     // dry) or only those of the window's first P.direct buckets.
     __device__ SSSP_NOINLINE void stage_flush(bool all) {
-        if (!P.stage) return;
-        unsigned long long win = 0;
-        if (lane == 0) win = window();
-        const uint32_t W = (uint32_t)__shfl_sync(kFull, win, 0);
+        if (!P.stage || (!all && P.direct == 0u)) return;
+        const uint32_t W = window_hint();
         for (int guard = 0; guard < 64; guard++) {
             // unlocked look for a non-empty candidate bucket
             uint32_t cnt = 0;
@@ -1675,9 +1711,7 @@ struct Worker {
 
     __device__ SSSP_NOINLINE void far_flush(uint32_t upto) {
         if (nfar <= upto) return;
-        unsigned long long win = 0;
-        if (P.stage && lane == 0) win = window();
-        const uint32_t W = (uint32_t)__shfl_sync(kFull, win, 0);
+        const uint32_t W = P.stage ? window_hint() : 0u;
         while (nfar > upto) {
             const uint32_t take = nfar - upto < 32u ? nfar - upto : 32u;
             const bool v = lane < take;
@@ -1830,7 +1864,7 @@ struct Worker {
     __device__ __forceinline__ void push_round(bool imp, uint32_t key, uint32_t nd, uint32_t w, uint32_t front,
                                                uint32_t& n_imp, uint32_t& n_mark) {
         n_imp += (uint32_t)__popc(__ballot_sync(kFull, imp));
-        if (P.pend) {
+        if (X && P.pend) {
             // an improved vertex already queued at an earlier-or-equal bucket
             // is not queued again: its queued element is relaxed with the
             // distance current when it is read
@@ -1842,7 +1876,7 @@ struct Worker {
             n_mark += (uint32_t)__popc(__ballot_sync(kFull, imp && !q));
             imp = q;
         }
-        if (P.dedup) {
+        if (X && P.dedup) {
             // in-warp duplicates (Listing 1's write of a warp's improved
             // vertices): lanes whose arcs improved the same target this round
             // are matched; one write per target is enough, the one with the
@@ -1862,7 +1896,7 @@ struct Worker {
         // a shadow vertex (a slice of a hub's arcs) always goes to L2 so that
         // the slices of one hub spread over all blocks
         const bool inside = MQ && P.qoff ? abs_bucket(key, nd) <= front : nd <= front;
-        const bool nearv = imp && !P.l2_only && w <= P.near_w && inside && key_vertex(key) < (uint32_t)P.n;
+        const bool nearv = imp && (!X || !P.l2_only) && w <= P.near_w && inside && key_vertex(key) < (uint32_t)P.n;
         const uint32_t m = __ballot_sync(kFull, nearv);
         if (m) {
             if (nearv) scratch()[__popc(m & lanemask_lt())] = make_uint2(key, nd);
@@ -1921,7 +1955,7 @@ struct Worker {
             raise_error(P.ctrl, kErrElement, 8, (int)key);
             valid = false;
         }
-        if (valid && P.pend) {
+        if (X && valid && P.pend) {
             // pending marks: the read takes the vertex's mark; a mark already
             // taken by an earlier read means no improvement since that read's
             // relaxation, so the element is stale.  Otherwise the arcs are
@@ -2000,7 +2034,7 @@ struct Worker {
         const uint32_t dm = __ballot_sync(kFull, defer);
         if (dm) {
             // a deferred vertex is queued again (in L0): it gets its mark back
-            if (defer && P.pend) atomicMin(P.pend + dist_index(key), abs_bucket(key, el.y));
+            if (X && defer && P.pend) atomicMin(P.pend + dist_index(key), abs_bucket(key, el.y));
             if (defer) scratch()[__popc(dm & lanemask_lt())] = el;
             __syncwarp();
             l0_push(__popc(dm), true);
@@ -2024,9 +2058,7 @@ struct Worker {
         // every write is local (near_deltas = 0, as in Listing 1)
         uint32_t front = kInfU32;
         if (SSSP_FRONT_BOUND && P.near_w != kInfU32) {
-            unsigned long long win = 0;
-            if (lane == 0) win = window();
-            const uint32_t W = (uint32_t)__shfl_sync(kFull, win, 0);
+            const uint32_t W = window_hint();
             front = MQ && P.qoff ? W + (uint32_t)P.filter_deltas : A::upper(W, P.delta, P.filter_deltas);
         }
         // predecessor id: a shadow vertex stands for its owner
@@ -2116,7 +2148,7 @@ struct Worker {
         for (;;) {
             mark(1, iter);
             stat(kStIter, 1);
-            if (P.timeline && blockIdx.x == 0 && threadIdx.x == 0) sample();
+            if (X && P.timeline && blockIdx.x == 0 && threadIdx.x == 0) sample();
             if ((++iter & 7u) == 0 || idle_ns || P.slice_ns) {
                 int stop = 0;
                 if (lane == 0) {
@@ -2179,14 +2211,14 @@ struct Worker {
             }
             idle_ns = 0;
             mark(7, iter);
-            if (P.timeline) {
+            if (X && P.timeline) {
                 // run-time sampling only: the batch's elements, and block 0's busy warps
                 const uint32_t nb = (uint32_t)__popc(__ballot_sync(kFull, valid));
                 if (lane == 0) atomicAdd(&P.ctrl->processed, (unsigned long long)nb);
                 if (blockIdx.x == 0 && lane == 0) atomicAdd(&S()->busy, 1u);
             }
             dec += relax_batch(valid, e);
-            if (P.timeline && blockIdx.x == 0 && lane == 0) atomicSub(&S()->busy, 1u);
+            if (X && P.timeline && blockIdx.x == 0 && lane == 0) atomicSub(&S()->busy, 1u);
             stat(kCyRelax, (unsigned long long)((unsigned long long)(clock64() - c3)));
             mark(10, iter);
             acct_apply();
@@ -2270,12 +2302,16 @@ struct Worker {
     }
 };
 
-template <int WT, int PRED, bool MQ, int R>
 // The parameters are a grid constant (no local copy is made when their
 // address is taken); the prologue copies them to shared memory, from where
 // the workers read them: with a local copy every field read was a
 // local-memory load, and through the grid constant the out-of-line queue
 // functions read them with generic loads.
+// X: the extended kernel, with the optional paths (pending marks, the
+// in-warp duplicate filter, the single-queue baseline, run-time sampling,
+// the debug trace).  X = false compiles them out: a smaller kernel, which
+// runs every configuration that uses none of them.
+template <int WT, int PRED, bool MQ, int R, bool X>
 __global__ void __launch_bounds__(1024, 1) mlmq_kernel(const __grid_constant__ KParams P) {
     BlockShared* S = reinterpret_cast<BlockShared*>(mlmq_smem);
     volatile uint2* l1 = reinterpret_cast<volatile uint2*>(mlmq_smem + P.l1_off);
@@ -2289,6 +2325,7 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(const __grid_constant__ K
         for (int i = 0; i < 32; i++) S->scnt[i] = S->shead[i] = 0;
         unsigned long long win = ld_acquire64(&P.ctrl->window);
         S->nf = Arith<WT>::upper((uint32_t)win, P.delta, 1.0f);
+        S->wcache = (uint32_t)win;
         S->deadline = gtime() + P.timeout_ns;
         S->t0 = gtime();
         S->next_sample = 0;
@@ -2313,7 +2350,7 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(const __grid_constant__ K
         for (int i = threadIdx.x; i < (int)(sizeof(KParams) / 4); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    Worker<WT, PRED, MQ, R> w(S->params);
+    Worker<WT, PRED, MQ, R, X> w(S->params);
     w.run();
     if (P.slice_ns) {
         // serving slice: every warp has drained its private state; one warp
