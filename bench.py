@@ -362,7 +362,8 @@ def road_leg(S, gg, torch, nsrc: int = 4, tune_ms: int = 3000):
             out[name] = {"ms_per_solve": round(float(np.mean(ms)), 3),
                          "gteps": round(arcs / (sum(ms) / 1e3) / 1e9, 3),
                          "config": {k: v for k, v in cfg.as_dict().items()
-                                    if k in ("l1_type", "delta_u32", "bnum", "near_deltas", "block_threads")}}
+                                    if k not in ("delta_f32", "l0_rows", "timeout_ms", "pending_marks",
+                                                 "dedup", "l2_only")}}
         return out
     finally:
         G.close()

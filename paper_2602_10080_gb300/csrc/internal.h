@@ -28,10 +28,12 @@ SSSP_DECLARE_INSTANCES(f32)
 SSSP_DECLARE_INSTANCES(f32x)
 #undef SSSP_DECLARE_INSTANCES
 
-// The extended kernel runs a launch that uses one of the optional paths; the
-// lean one (compiled without them) runs every other launch.
+// The extended kernel runs a launch that uses one of the optional paths (or
+// an L1 policy with a block lock: near-far, SLF); the lean one, compiled
+// without them, runs every other launch.
 inline bool needs_extended(const KParams& p) {
-    return p.pend != nullptr || p.dedup != 0 || p.l2_only != 0 || p.timeline != nullptr || p.trace != nullptr;
+    return p.pend != nullptr || p.dedup != 0 || p.l2_only != 0 || p.timeline != nullptr || p.trace != nullptr ||
+           p.l1_type == 1 /* near-far */ || p.l1_type == 3 /* SLF */;
 }
 
 inline cudaError_t launch_mlmq(const KernelKey& key, dim3 grid, dim3 block, size_t smem,

@@ -676,12 +676,20 @@ struct Worker {
     // the block's copy; window_hint() returns the copy, for decisions that
     // only group or route elements (the staging bucket, the local front, the
     // L1 filter), where a slightly stale base costs nothing.
+#ifndef SSSP_WIN_HINT
+#define SSSP_WIN_HINT 1
+#endif
+#if SSSP_WIN_HINT
     __device__ __forceinline__ unsigned long long window() const {
         const unsigned long long w = ld_relaxed64(&P.ctrl->window);
         S()->wcache = (uint32_t)w;
         return w;
     }
     __device__ __forceinline__ uint32_t window_hint() const { return *(volatile uint32_t*)&S()->wcache; }
+#else
+    __device__ __forceinline__ unsigned long long window() const { return ld_acquire64(&P.ctrl->window); }
+    __device__ __forceinline__ uint32_t window_hint() const { return (uint32_t)ld_acquire64(&P.ctrl->window); }
+#endif
     __device__ __forceinline__ uint32_t home_shard() const {
         return (blockIdx.x + (threadIdx.x >> 5)) & (uint32_t)(P.shards - 1);
     }
@@ -1065,7 +1073,8 @@ struct Worker {
     // head (bounded by tail) and withdraw from each once it is full.  Both
     // waits are on warps that are already inside the same operation, so they
     // are short; they are bounded by the deadline.
-    __device__ __forceinline__ bool l1_lockfree() const { return P.l1_type == 0 || P.l1_type == 2; }
+    // the lean kernel (X = false) runs the lock-free policies only
+    __device__ __forceinline__ bool l1_lockfree() const { return !X || P.l1_type == 0 || P.l1_type == 2; }
 
     template <int K>
     __device__ void l1_write_lf(uint2 (&e)[K], bool (&valid)[K], int count_add, uint32_t fthr) {
@@ -1212,7 +1221,7 @@ struct Worker {
         uint32_t any = 0;
         if (lane == 0) {
             any = *(volatile uint32_t*)&S()->head != *(volatile uint32_t*)&S()->tail;
-            if (P.l1_type == 1) any |= *(volatile uint32_t*)&S()->fhead != *(volatile uint32_t*)&S()->ftail;
+            if (X && P.l1_type == 1) any |= *(volatile uint32_t*)&S()->fhead != *(volatile uint32_t*)&S()->ftail;
         }
         if (!__shfl_sync(kFull, any, 0)) return false;
         if (l1_lockfree()) return l1_read_lf(valid, e);
@@ -1273,7 +1282,7 @@ struct Worker {
         uint32_t f = 0;
         if (lane == 0) {
             uint32_t h = *(volatile uint32_t*)&S()->head, t = *(volatile uint32_t*)&S()->tail;
-            uint32_t cap = (uint32_t)P.l1_cap >> (P.l1_type == 1 ? 1 : 0);
+            uint32_t cap = (uint32_t)P.l1_cap >> (X && P.l1_type == 1 ? 1 : 0);
             uint32_t used = t - h;
             f = used < cap ? cap - used : 0u;
         }
@@ -2309,8 +2318,9 @@ struct Worker {
 // functions read them with generic loads.
 // X: the extended kernel, with the optional paths (pending marks, the
 // in-warp duplicate filter, the single-queue baseline, run-time sampling,
-// the debug trace).  X = false compiles them out: a smaller kernel, which
-// runs every configuration that uses none of them.
+// the debug trace, the L1 policies with a block lock).  X = false compiles
+// them out: a smaller kernel, which runs every configuration that uses none
+// of them.
 template <int WT, int PRED, bool MQ, int R, bool X>
 __global__ void __launch_bounds__(1024, 1) mlmq_kernel(const __grid_constant__ KParams P) {
     BlockShared* S = reinterpret_cast<BlockShared*>(mlmq_smem);
