@@ -64,6 +64,7 @@ constexpr int kChunk = 32;          // elements per L2 chunk
 #endif
 constexpr int kFarCap = SSSP_FAR_CAP;  // per-warp far staging (elements)
 constexpr int kMaxClaim = 16;       // chunks per L2 claim (upper bound, a power of two)
+constexpr int kDescCap = 64;  // claimed-chunk descriptors per block (a power of two)
 constexpr int kStageCap = SSSP_STAGE_CAP;  // block staging per L2 bucket (elements, a power of two >= 64)
 #ifndef SSSP_WINDOW_GUARD
 #define SSSP_WINDOW_GUARD 8
@@ -104,6 +105,7 @@ enum : int {
     kCyClaim,         // SSSP_FINE_CYCLES: l2_claim (window, probes, read-ticket CAS)
     kCyChunks,        // SSSP_FINE_CYCLES: waiting for and reading claimed chunks (incl. L1 writes)
     kCyStage,         // SSSP_FINE_CYCLES: stage_flush
+    kStPopL2Desc,     // claimed chunks read through a descriptor by another warp of the block
     kStCount
 };
 
@@ -263,6 +265,27 @@ __device__ __forceinline__ bool slot_try_take(volatile uint2* p, uint2& e) {
     return true;
 }
 
+// Mailbox slots of the descriptor ring: the deposit releases, and the
+// withdrawal acquires, at CTA scope, so that a warp that takes a descriptor
+// sees everything the depositing warp saw (the chunk it acquired in L2).
+__device__ __forceinline__ bool desc_try_put(unsigned long long* p, unsigned long long v) {
+    if (*(volatile unsigned long long*)p != kEmptySlot) return false;
+    unsigned long long old;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("atom.release.cta.shared::cta.cas.b64 %0, [%1], %2, %3;"
+                 : "=l"(old) : "r"(a), "l"(kEmptySlot), "l"(v) : "memory");
+    return old == kEmptySlot;
+}
+__device__ __forceinline__ bool desc_try_take(unsigned long long* p, unsigned long long& v) {
+    if (*(volatile unsigned long long*)p == kEmptySlot) return false;
+    unsigned long long old;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("atom.acquire.cta.shared::cta.exch.b64 %0, [%1], %2;" : "=l"(old) : "r"(a), "l"(kEmptySlot) : "memory");
+    if (old == kEmptySlot) return false;
+    v = old;
+    return true;
+}
+
 // Ticket w is ahead of ticket r (wrap-safe): some writer holds ticket r.
 // Any observed w with w - r > 0 proves ticket r was taken, whatever the order
 // in which the two relaxed loads were performed.
@@ -305,6 +328,12 @@ __device__ __forceinline__ bool ahead(uint32_t w, uint32_t r) { return (int32_t)
 // slower).
 #ifndef SSSP_PUB_FENCE
 #define SSSP_PUB_FENCE 0
+#endif
+#ifndef SSSP_CHUNK_DESC
+#define SSSP_CHUNK_DESC 1
+#endif
+#ifndef SSSP_CLAIM_HINT
+#define SSSP_CLAIM_HINT 0
 #endif
 #ifndef SSSP_NOINLINE
 #define SSSP_NOINLINE __noinline__
@@ -462,6 +491,8 @@ struct BlockShared {
     unsigned long long next_sample;
     uint32_t nsamples;
     uint32_t wcache;              // the window base as last read from ctrl.window by a warp of the block
+    uint32_t dhead, dtail;        // claimed-chunk descriptor ring (SSSP_CHUNK_DESC)
+    unsigned long long desc[kDescCap];  // (ticket << 32) | (count << 16) | ring, kEmptySlot = free
     uint32_t busy;                // warps of the block holding a batch (sampling only)
     KParams params;               // the launch parameters, read by the workers from here
 };
@@ -824,10 +855,19 @@ struct Worker {
     // rings: the first hub_bnum) with one CAS on its read ticket.  Returns the
     // number of chunks claimed (warp-uniform) with their ring and first ticket.
     __device__ uint32_t l2_claim(uint32_t want, uint32_t& ring_out, uint32_t& t_out) {
+#if SSSP_CLAIM_HINT
+        // the first probe starts from the block's copy of the window base
+        // while the current base is loaded; a stale copy means one more probe
+        unsigned long long win = 0;
+        if (lane == 0) win = ld_relaxed64(&P.ctrl->window);
+        uint32_t W = window_hint();
+        bool checked = false;
+#else
         unsigned long long win = 0;
         if (lane == 0) win = window();
         win = __shfl_sync(kFull, win, 0);
         const uint32_t W = (uint32_t)win;
+#endif
         const uint32_t S_ = (uint32_t)P.shards, per = 32u / S_;
         const uint32_t home = home_shard();
         for (uint32_t r0 = 0; r0 < (uint32_t)P.bmax; r0 += per) {
@@ -839,6 +879,18 @@ struct Worker {
                 r = ld_relaxed(P.l2.rt + (size_t)ring * 32);
                 w = ld_relaxed(P.l2.wt + (size_t)ring * 32);
             }
+#if SSSP_CLAIM_HINT
+            if (!checked) {
+                checked = true;
+                win = __shfl_sync(kFull, win, 0);
+                if ((uint32_t)win != W) {
+                    W = (uint32_t)win;
+                    if (lane == 0) S()->wcache = W;
+                    r0 = 0u - per;  // probe again from bucket W
+                    continue;
+                }
+            }
+#endif
             const bool ne = probe && ahead(w, r);
             const uint32_t nonempty = __ballot_sync(kFull, ne);
             if (nonempty == 0) continue;
@@ -910,10 +962,12 @@ struct Worker {
     }
 
     // Reads chunk t + j (count c) into the lanes and frees its slot.
+    // CG: load through L2 only (a chunk claimed by another warp of the block).
+    template <bool CG = false>
     __device__ void l2_read_chunk(uint32_t ring, uint32_t tj, uint32_t c, bool& valid, uint2& e) {
         const size_t slot = (size_t)ring * P.l2.nch + (tj & (P.l2.nch - 1u));
         valid = lane < c;
-        if (valid) e = P.l2.data[slot * kChunk + lane];
+        if (valid) e = CG ? __ldcg(P.l2.data + slot * kChunk + lane) : P.l2.data[slot * kChunk + lane];
         count_live(valid, e.x, -1);
         __syncwarp();
         if (lane == 0) {
@@ -1378,6 +1432,95 @@ struct Worker {
     // The first claimed chunk becomes this warp's batch, the rest go to L1.
     // Returns 1 with a batch in the lanes, 2 if only L1 received elements, 0
     // if L2 had nothing, -1 if enough warps of the block are already refilling.
+    // ---- claimed-chunk descriptors (SSSP_CHUNK_DESC) ------------------------
+    // A refill keeps the first claimed chunk as its own batch and hands the
+    // others to the block as descriptors (ring, ticket, count) instead of
+    // copying their elements into L1: another warp of the block takes a
+    // descriptor and reads the chunk itself, so the chunks of one claim are
+    // read by several warps at once, and their elements skip the L1 ring.
+    // The elements are in the block count from the claim on.
+    __device__ __forceinline__ uint32_t desc_free() const {
+        uint32_t f = 0;
+        if (lane == 0) {
+            const uint32_t used = *(volatile uint32_t*)&S()->dtail - *(volatile uint32_t*)&S()->dhead;
+            f = used < (uint32_t)kDescCap ? (uint32_t)kDescCap - used : 0u;
+        }
+        return __shfl_sync(kFull, f, 0);
+    }
+
+    // Deposits descriptors for chunks 1 .. got - 1 of a claim (lane j: the
+    // count of chunk j); returns k: chunks 1 .. k were handed over, the rest
+    // did not fit.
+    __device__ uint32_t desc_put(uint32_t ring, uint32_t t, uint32_t got, uint32_t cnt) {
+        uint32_t base = 0, take = 0;
+        if (lane == 0) {
+            uint32_t tl = *(volatile uint32_t*)&S()->dtail;
+            for (;;) {
+                const uint32_t h = *(volatile uint32_t*)&S()->dhead;
+                const uint32_t used = tl - h;
+                take = used < (uint32_t)kDescCap ? min(got - 1u, (uint32_t)kDescCap - used) : 0u;
+                if (take == 0) break;
+                const uint32_t old = atomicCAS(&S()->dtail, tl, tl + take);
+                if (old == tl) break;
+                tl = old;
+            }
+            base = tl;
+        }
+        take = __shfl_sync(kFull, take, 0);
+        base = __shfl_sync(kFull, base, 0);
+        if (lane >= 1u && lane <= take) {
+            const unsigned long long d = ((unsigned long long)(t + lane) << 32) | (unsigned long long)(ring | (cnt << 16));
+            unsigned long long* sl = &S()->desc[(base + lane - 1u) & (uint32_t)(kDescCap - 1)];
+            uint32_t spins = 0;
+            while (!desc_try_put(sl, d)) {
+                if ((++spins & 255u) == 0 && expired()) {
+                    raise_error(P.ctrl, kErrTimeout, 15, 0);
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+        return take;
+    }
+
+    // Takes one descriptor and reads its chunk into the lanes (the warp's
+    // batch).  False if there is none.
+    __device__ bool desc_read(bool& valid, uint2& e) {
+        valid = false;
+        uint32_t h = 0;
+        int got = 0;
+        if (lane == 0) {
+            h = *(volatile uint32_t*)&S()->dhead;
+            for (;;) {
+                if (*(volatile uint32_t*)&S()->dtail == h) break;
+                const uint32_t old = atomicCAS(&S()->dhead, h, h + 1u);
+                if (old == h) {
+                    got = 1;
+                    break;
+                }
+                h = old;
+            }
+        }
+        if (!__shfl_sync(kFull, got, 0)) return false;
+        unsigned long long d = kEmptySlot;
+        if (lane == 0) {
+            unsigned long long* sl = &S()->desc[h & (uint32_t)(kDescCap - 1)];
+            uint32_t spins = 0;
+            while (!desc_try_take(sl, d)) {
+                if ((++spins & 255u) == 0 && expired()) {
+                    raise_error(P.ctrl, kErrTimeout, 16, 0);
+                    break;
+                }
+            }
+        }
+        d = __shfl_sync(kFull, d, 0);
+        if (d == kEmptySlot) return true;  // timed out: the error stops the launch
+        const uint32_t lo = (uint32_t)d;
+        l2_read_chunk<true>(lo & 0xffffu, (uint32_t)(d >> 32), lo >> 16, valid, e);
+        stat(kStPopL2Desc, 1);
+        return true;
+    }
+
     __device__ int refill(bool& valid, uint2& e) {
         valid = false;
         int role = 0;
@@ -1396,7 +1539,8 @@ struct Worker {
         stage_flush(false);
 #endif
         uint32_t want = (uint32_t)P.claim;
-        const uint32_t room = l1_free() / kChunk;
+        uint32_t room = l1_free() / kChunk;
+        if (SSSP_CHUNK_DESC) room = max(room, desc_free());
         if (want > room + 1u) want = room + 1u;
         uint32_t ring = 0, t = 0;
 #if SSSP_FINE_CYCLES
@@ -1420,7 +1564,8 @@ struct Worker {
                 const uint32_t c0 = __shfl_sync(kFull, cnt, 0);
                 if (!(SSSP_BULK_REFILL && got > 1 && l1_lockfree() && read_chunks_bulk(ring, t, got, cnt, valid, e))) {
                     l2_read_chunk(ring, t, c0, valid, e);
-                    for (uint32_t j = 1; j < got; j++) {
+                    const uint32_t j0 = SSSP_CHUNK_DESC && got > 1u ? 1u + desc_put(ring, t, got, cnt) : 1u;
+                    for (uint32_t j = j0; j < got; j++) {
                         const uint32_t cj = __shfl_sync(kFull, cnt, j);
                         bool v2 = false;
                         uint2 x[1] = {make_uint2(0, 0)};
@@ -2179,6 +2324,7 @@ struct Worker {
             const long long c1 = clock64();
             stat(kCyL0, (unsigned long long)((unsigned long long)(c1 - c0)));
             if (!got) got = l1_read(valid, e);
+            if (SSSP_CHUNK_DESC && !got) got = desc_read(valid, e);
             const long long c2 = clock64();
             int rf = 1;
             if (!got) {
@@ -2261,6 +2407,15 @@ struct Worker {
     // and the block staging to L2, then publish the block's count.
     __device__ __noinline__ void drain_block() {
         if (ld_volatile_int(&P.ctrl->error) != 0) return;
+        if (SSSP_CHUNK_DESC) {
+            // claimed chunks not read yet go back to L2
+            bool v = false;
+            uint2 x = make_uint2(0, 0);
+            while (desc_read(v, x)) {
+                dec += l2_write(v, x);
+                if (ld_volatile_int(&P.ctrl->error) != 0) return;
+            }
+        }
         if (l1_lockfree()) {
             bool v = false;
             uint2 x = make_uint2(0, 0);
@@ -2322,7 +2477,13 @@ struct Worker {
 // them out: a smaller kernel, which runs every configuration that uses none
 // of them.
 template <int WT, int PRED, bool MQ, int R, bool X>
-__global__ void __launch_bounds__(1024, 1) mlmq_kernel(const __grid_constant__ KParams P) {
+#ifndef SSSP_LB_THREADS
+#define SSSP_LB_THREADS 1024
+#endif
+#ifndef SSSP_LB_MIN_BLOCKS
+#define SSSP_LB_MIN_BLOCKS 1
+#endif
+__global__ void __launch_bounds__(SSSP_LB_THREADS, SSSP_LB_MIN_BLOCKS) mlmq_kernel(const __grid_constant__ KParams P) {
     BlockShared* S = reinterpret_cast<BlockShared*>(mlmq_smem);
     volatile uint2* l1 = reinterpret_cast<volatile uint2*>(mlmq_smem + P.l1_off);
     if (threadIdx.x == 0) {
@@ -2336,6 +2497,8 @@ __global__ void __launch_bounds__(1024, 1) mlmq_kernel(const __grid_constant__ K
         unsigned long long win = ld_acquire64(&P.ctrl->window);
         S->nf = Arith<WT>::upper((uint32_t)win, P.delta, 1.0f);
         S->wcache = (uint32_t)win;
+        S->dhead = S->dtail = 0;
+        for (int i = 0; i < kDescCap; i++) S->desc[i] = kEmptySlot;
         S->deadline = gtime() + P.timeout_ns;
         S->t0 = gtime();
         S->next_sample = 0;

@@ -854,8 +854,9 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
                          hc.stats[kCyL1], hc.stats[kCyL2Write], hc.stats[kCyGlobalRead], hc.stats[kCyIdle],
                          hc.stats[kCyL0]);
         if (dbg > 1)
-            std::fprintf(stderr, "[sssp]   window pull-backs %llu advances %llu elements written to buckets 0-1 %llu\n",
-                         hc.stats[kStPullBack], hc.stats[kStAdvance], hc.stats[kStLowWrite]);
+            std::fprintf(stderr, "[sssp]   window pull-backs %llu advances %llu elements written to buckets 0-1 %llu "
+                                 "chunks read through descriptors %llu\n",
+                         hc.stats[kStPullBack], hc.stats[kStAdvance], hc.stats[kStLowWrite], hc.stats[kStPopL2Desc]);
         if (hc.error == kErrNone && hc.finished) return SSSP_OK;
         if (dbg)
             std::fprintf(stderr, "[sssp] solve failed: error=%d where=%d info=%d finished=%d reserve=%llu done=%llu "
