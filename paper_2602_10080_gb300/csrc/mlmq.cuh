@@ -63,7 +63,7 @@ constexpr int kChunk = 32;          // elements per L2 chunk
 #define SSSP_STAGE_CAP 64
 #endif
 constexpr int kFarCap = SSSP_FAR_CAP;  // per-warp far staging (elements)
-constexpr int kMaxClaim = 16;       // chunks per L2 claim (upper bound, a power of two)
+constexpr int kMaxClaim = 32;       // chunks per L2 claim (upper bound, a power of two <= 32)
 constexpr int kDescCap = 64;  // claimed-chunk descriptors per block (a power of two)
 constexpr int kStageCap = SSSP_STAGE_CAP;  // block staging per L2 bucket (elements, a power of two >= 64)
 #ifndef SSSP_WINDOW_GUARD

@@ -51,7 +51,10 @@ sssp_config prior_config(const Graph* g) {
             c.filter_deltas = 1.0f;
             c.near_deltas = 1.0f;
             c.bnum = 16;
-            c.claim = 8;   // many small buckets of work: fewer, larger L2 reads
+            // many small buckets of work: fewer, larger L2 reads (16 chunks, of which the
+            // refilling warp reads one and other warps the rest: R-MAT-22 on GB300 3.16 ms
+            // against 3.53 with 8 and 3.28 with 32)
+            c.claim = 16;
             // hub slices of 512 arcs: with each slice relaxed from its hub's current
             // distance, R-MAT-22 took 6.8 ms against 8.0 ms with 1024 (relaxations
             // 237M -> 178M; 384: 7.0, 768: 6.9, 256: 8.3 ms) on GB300
@@ -97,6 +100,7 @@ sssp_config prior_config(const Graph* g) {
         c.blocks_per_sm = 1;
         c.shards = 16;
         c.refillers = 4;
+        c.claim = 8;  // 15.4-15.7 ms against 16.0 with 4
     }
     if (family_of(f) == kPowerLaw) {
         // a quarter of the general width with 16 active buckets (the same
@@ -207,7 +211,7 @@ extern "C" int sssp_autotune(sssp_graph* gh, const int32_t* srcs, int32_t nsrc, 
             c.shards = sh;
             cands.push_back(c);
         }
-        for (int cl : {4, 8, 16}) {
+        for (int cl : {4, 8, 16, 32}) {
             sssp_config c = best;
             if (c.claim == cl) continue;
             c.claim = cl;
@@ -335,7 +339,7 @@ extern "C" int sssp_autotune_batch(sssp_graph* gh, const int32_t* srcs, int32_t 
                 c.l1_cap = l1;
                 cands.push_back(c);
             }
-            for (int cl : {4, 8, 16}) {
+            for (int cl : {4, 8, 16, 32}) {
                 sssp_config c = best;
                 c.claim = cl;
                 cands.push_back(c);
