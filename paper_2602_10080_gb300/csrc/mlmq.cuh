@@ -171,6 +171,7 @@ struct KParams {
                              // non-empty buckets; 0: they share the rings
     int32_t dedup;           // 1: one write per improved target of a warp round
     uint32_t direct;         // block staging: writes to the window's first `direct` buckets go to L2 at once
+    int32_t desc;            // 1: claimed chunks beyond the first go to the block as descriptors (else into L1)
     uint32_t* pend;          // pending marks (or null): per distance slot, the lowest bucket at which
                              // the vertex has a queued element, kInfU32 = none (see relax_batch)
     int32_t scratch_off, far_off, stat_off, stage_off, l1_off;  // byte offsets in dynamic shared memory
@@ -1540,7 +1541,7 @@ struct Worker {
 #endif
         uint32_t want = (uint32_t)P.claim;
         uint32_t room = l1_free() / kChunk;
-        if (SSSP_CHUNK_DESC) room = max(room, desc_free());
+        if (SSSP_CHUNK_DESC && P.desc) room = max(room, desc_free());
         if (want > room + 1u) want = room + 1u;
         uint32_t ring = 0, t = 0;
 #if SSSP_FINE_CYCLES
@@ -1564,7 +1565,7 @@ struct Worker {
                 const uint32_t c0 = __shfl_sync(kFull, cnt, 0);
                 if (!(SSSP_BULK_REFILL && got > 1 && l1_lockfree() && read_chunks_bulk(ring, t, got, cnt, valid, e))) {
                     l2_read_chunk(ring, t, c0, valid, e);
-                    const uint32_t j0 = SSSP_CHUNK_DESC && got > 1u ? 1u + desc_put(ring, t, got, cnt) : 1u;
+                    const uint32_t j0 = SSSP_CHUNK_DESC && P.desc && got > 1u ? 1u + desc_put(ring, t, got, cnt) : 1u;
                     for (uint32_t j = j0; j < got; j++) {
                         const uint32_t cj = __shfl_sync(kFull, cnt, j);
                         bool v2 = false;

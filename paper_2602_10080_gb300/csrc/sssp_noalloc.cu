@@ -256,6 +256,7 @@ extern "C" int sssp_solve_noalloc(const int32_t* row_ptr, const uint32_t* arcs, 
     P.refillers = 4;
     P.stage = 1;
     P.direct = 2;
+    P.desc = 1;
     P.scratch_off = (int32_t)scratch_off;
     P.far_off = (int32_t)far_off;
     P.stat_off = (int32_t)stat_off;
