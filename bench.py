@@ -66,8 +66,8 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-TRAFFIC_CONFIG_KEYS = ("l1_type", "l2_type", "delta_u32", "bnum", "bmax", "claim", "block_threads", "split_arcs",
-                       "hub_bnum", "pending_marks")
+TRAFFIC_CONFIG_KEYS = ("l1_type", "l2_type", "delta_u32", "bnum", "bmax", "claim", "shards", "block_threads",
+                       "split_arcs", "hub_bnum", "pending_marks", "direct_buckets")
 
 
 def config_signature(cfg) -> str:
@@ -619,9 +619,9 @@ def main():
                    "n": g.n, "m": g.m, "giant": giant, "l2_flush": l2_note,
                    "l2_residency": l2_res,
                    "queue": {k: v for k, v in tuned.as_dict().items()
-                             if k in ("l1_type", "l2_type", "delta_u32", "bnum", "bmax", "wb", "claim",
+                             if k in ("l1_type", "l2_type", "delta_u32", "bnum", "bmax", "wb", "claim", "shards",
                                       "filter_deltas", "th_heavy", "block_threads", "split_arcs",
-                                      "hub_bnum")},
+                                      "hub_bnum", "direct_buckets")},
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": round(e2e_value, 3), "unit": "GTEPS", "h2d_bytes_per_step": 4,
                 "d2h_bytes_per_step": 8 * g.n},
