@@ -99,6 +99,10 @@ int plan_launch(const Graph* g, const sssp_config& cfg, int pred_mode, bool mq, 
 bool is_device_ptr(const void* p);
 void resolve_auto(const Graph* g, sssp_config* c);
 void batch_delta(const Graph* g, sssp_config* c, int div);   // delta / div for multi-query launches
+// The library's configuration of a multi-query launch of nq queries (the
+// caller's config otherwise untouched): narrower buckets, fewer active ones
+// (sssp_autotune.cu).
+void batch_config(const Graph* g, sssp_config* c, int32_t nq);
 // Size class of a multi-query launch (nq rounded down to a power of two).
 int32_t nq_class(int32_t nq);
 // The batch-tuned configuration for nq queries (same size class), or null.

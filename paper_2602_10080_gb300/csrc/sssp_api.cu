@@ -594,10 +594,7 @@ int run_queries(Graph* g, const int32_t* srcs_host, const int32_t* srcs_dev, int
     if (unit && (!cfg_in || cfg.delta_u32 == 0)) cfg.delta_u32 = 1;
     const bool lib_delta = !cfg_in || (g->wtype == SSSP_W_F32 ? !(cfg_in->delta_f32 > 0.0f) : cfg_in->delta_u32 == 0);
     resolve_auto(g, &cfg);
-    if (nq > 1 && !unit && lib_delta) {
-        batch_delta(g, &cfg, std::min(16, std::max(1, nq / 32)));
-        cfg.bnum = std::min(cfg.bnum, 4);   // the batch width was measured with 4 active buckets
-    }
+    if (nq > 1 && !unit && lib_delta) batch_config(g, &cfg, nq);
     int rc = validate_config(&cfg);
     if (rc) return rc;
     if (cudaSetDevice(g->device) != cudaSuccess) return SSSP_E_CUDA;

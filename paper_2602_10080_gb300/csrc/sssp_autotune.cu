@@ -39,6 +39,21 @@ static Family family_of(const sssp_features& f) {
     return kMesh;
 }
 
+void batch_config(const Graph* g, sssp_config* c, int32_t nq) {
+    int div = std::min(16, std::max(1, nq / 32));
+    int bnum = 4;   // the batch width was measured with 4 active buckets
+    if (family_of(g->feat) == kPowerLaw && g->wtype == SSSP_W_U32) {
+        // integer weights on a power-law graph: half the narrowing, 8 active buckets.  256
+        // R-MAT-20 sources on GB300 (1024-thread blocks): 141 ms against 145 ms with
+        // delta / 8 and 4 buckets; fp32 weights were slower with wider buckets (229 ms
+        // against 199 ms), so they keep delta / 8
+        div = std::max(1, div / 2);
+        bnum = 8;
+    }
+    batch_delta(g, c, div);
+    c->bnum = std::min(c->bnum, bnum);
+}
+
 sssp_config prior_config(const Graph* g) {
     sssp_config c;
     sssp_config_default(&c);
@@ -66,6 +81,9 @@ sssp_config prior_config(const Graph* g) {
             // 16 rings per bucket: fewer refills contend for one ring's read ticket
             // (R-MAT-22 on GB300: 4.70 ms against 4.93 with 8; 32: 5.31 ms)
             c.shards = 16;
+            // one block of 1024 threads per SM: R-MAT-22 3.06 ms against 3.17 with two of
+            // 512, and 256 R-MAT-20 sources in one launch 145 ms against 152
+            c.block_threads = 1024;
             break;
         case kMesh:
             c.l1_type = SSSP_L1_FILTER;
@@ -222,8 +240,9 @@ extern "C" int sssp_autotune(sssp_graph* gh, const int32_t* srcs, int32_t nsrc, 
             c.max_arcs = ma;
             cands.push_back(c);
         }
-        for (int bt : {256, 1024}) {
+        for (int bt : {256, 512, 1024}) {
             sssp_config c = best;
+            if (c.block_threads == bt) continue;
             c.block_threads = bt;
             cands.push_back(c);
         }
@@ -296,9 +315,7 @@ extern "C" int sssp_autotune_batch(sssp_graph* gh, const int32_t* srcs, int32_t 
     base.delta_u32 = 0;
     base.delta_f32 = 0.0f;
     resolve_auto(g, &base);
-    const int div0 = std::min(16, std::max(1, nq / 32));
-    batch_delta(g, &base, div0);
-    base.bnum = std::min(base.bnum, 4);
+    batch_config(g, &base, nq);
     sssp_config best = base;
     if (budget_ms > 0) {
         void* dbuf = nullptr;
@@ -329,9 +346,23 @@ extern "C" int sssp_autotune_batch(sssp_graph* gh, const int32_t* srcs, int32_t 
                 else c.delta_u32 = (uint32_t)std::max(1.0, std::floor(d1 / div));
                 cands.push_back(c);
             }
-            for (int bn : {1, 2, 4, 8}) {
+            for (int bn : {1, 2, 4, 8, 16}) {
                 sssp_config c = best;
                 c.bnum = bn;
+                cands.push_back(c);
+            }
+            // bucket width and active buckets together (a wider bucket wants more of them)
+            for (int div : {2, 4}) {
+                sssp_config c = best;
+                if (f32) c.delta_f32 = (float)(d1 / div);
+                else c.delta_u32 = (uint32_t)std::max(1.0, std::floor(d1 / div));
+                c.bnum = 16;
+                cands.push_back(c);
+            }
+            for (int bt : {512, 1024}) {
+                sssp_config c = best;
+                if (c.block_threads == bt) continue;
+                c.block_threads = bt;
                 cands.push_back(c);
             }
             for (int l1 : {1024, 2048, 4096}) {

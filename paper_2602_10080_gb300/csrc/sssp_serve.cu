@@ -523,6 +523,8 @@ Lane* lane_create(sssp_server* s, Graph* g, int pred_mode, int* rc) {
             resolve_auto(g, &cfg);
             batch_delta(g, &cfg, 4);   // without one: narrower buckets
             cfg.bnum = std::min(cfg.bnum, 4);
+            // lanes were measured with 512-thread blocks (several lanes share the SMs)
+            cfg.block_threads = 512;
         }
         *rc = validate_config(&cfg);
         if (!*rc) *rc = plan_launch(g, cfg, pred_mode, true, &L->plan);
