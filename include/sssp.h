@@ -113,7 +113,9 @@ typedef struct sssp_config {
                               <= near_deltas * delta, to a distance <= F, enters L0/L1; any other
                               goes to its L2 bucket (0 = every write enters L0, as in Listing 1) */
     int32_t max_arcs;      /* arcs one warp relaxes per batch; later vertices wait in L0 (>= 32) */
-    int32_t claim;         /* L2 chunks one L1 refill claims at once (1..32) */
+    int32_t claim;         /* L2 chunks one refill claims at once (1..32): the refilling warp
+                              reads the first, the others go to its block (as descriptors that
+                              other warps read, or into L1 for breadth-first search) */
     int32_t shards;        /* rings per L2 bucket (1, 2, 4, 8, 16 or 32) */
     int32_t refillers;     /* warps of one block that may refill L1 from L2 at the same time (1..32) */
     int32_t stage;         /* 1: a block pools heavy-arc writes per L2 bucket in shared memory and

@@ -89,7 +89,9 @@ def with_hubs(g, hubs, seed):
 def test_random_graphs_stress(seed):
     """Tiny queue capacities force constant spill/refill; a 32-arc hub split
     threshold turns every vertex above 32 arcs (the planted hubs) into
-    shadow vertices, with and without their own hub rings."""
+    shadow vertices, with and without their own hub rings.  Claims of up to
+    32 chunks go to the block as descriptors (the 256-slot L1 would hold 8),
+    and 0-3 front buckets bypass the block staging."""
     rng = np.random.default_rng(seed)
     n = int(rng.integers(1, 3000))
     m = int(rng.integers(0, 12 * n))
@@ -101,7 +103,8 @@ def test_random_graphs_stress(seed):
     c = cfg(l1_type=L1_ALL[seed % 4], l2_type=seed % 2, l1_cap=256, bmax=int(rng.choice([1, 2, 8, 32])),
             bnum=int(rng.choice([1, 2, 4])), split_arcs=32, hub_bnum=int(rng.choice([0, 1, 2])),
             dedup=int(seed % 2), wb=int(rng.choice([0, 1, 4])), block_threads=int(rng.choice([256, 512, 1024])),
-            pending_marks=int(seed % 5 == 0))
+            pending_marks=int(seed % 5 == 0), claim=int(rng.choice([1, 4, 16, 32])),
+            direct_buckets=int(rng.choice([0, 1, 2, 3])), shards=int(rng.choice([2, 4, 16])))
     if wt == "u32":
         c.delta_u32 = int(rng.integers(1, 200))
     else:
