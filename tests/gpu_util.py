@@ -17,7 +17,7 @@ def cfg(**kw):
     that is not a field of sssp_config raises (ctypes would accept any
     attribute name silently)."""
     c = S.sssp_config_default()
-    fields = {name for name, _ in S.sssp_config._fields_} - {"reserved"}
+    fields = {name for name, _ in S.sssp_config._fields_}
     for k, v in kw.items():
         if k not in fields:
             raise KeyError(f"sssp_config has no field {k!r}")

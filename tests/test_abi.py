@@ -74,6 +74,10 @@ def test_host_only_calls(lib):
     assert lib.sssp_version() >= 10000
     c = sssp.sssp_config_default()
     assert c.l0_rows == 2 and c.block_threads in (256, 512, 1024)
+    # defaults: the first two buckets of the window bypass the block staging,
+    # claims within the 1..32 chunks a refill can hand over
+    assert c.direct_buckets == 2 and 1 <= c.claim <= 32
+    assert c.stage == 1 and c.split_arcs == 0 and c.pending_marks == 0
     assert lib.sssp_config_default(None) == sssp.SSSP_E_INVAL
     assert lib.sssp_graph_destroy(None) == sssp.SSSP_OK
 

@@ -234,6 +234,12 @@ def test_invalid_inputs():
     with pytest.raises(S.SsspError) as ei:
         G.solve(0, d, cfg=cfg(l1_cap=300))
     assert ei.value.code == S.SSSP_E_INVAL
+    for bad in (dict(claim=0), dict(claim=33), dict(direct_buckets=-1), dict(direct_buckets=33),
+                dict(shards=3), dict(block_threads=768)):
+        with pytest.raises(S.SsspError) as ei:
+            G.solve(0, d, cfg=cfg(**bad))
+        assert ei.value.code == S.SSSP_E_INVAL, bad
+    G.solve(0, d, cfg=cfg(claim=32, direct_buckets=32))   # the bounds themselves are valid
 
 
 def test_watchdog_timeout_then_recovers():
