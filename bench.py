@@ -499,6 +499,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="mlmq", choices=["mlmq", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving/cpu legs")
+    ap.add_argument("--legs", default="cpu,batch,bfs,road,queues,serving",
+                    help="extra legs to run after the metric (comma list; --no-extras runs none)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tune-ms", type=int, default=0,
                     help="timed autotune budget in ms (0 = the feature-based prior configuration)")
@@ -638,7 +640,8 @@ def main():
                  "cas_fail_per_refill": round(work_sum["cas_fail"] / max(1, work_sum["refills"]), 2),
                  "grid_blocks": stats["grid_blocks"], "block_threads": stats["block_threads"]},
     }
-    if rank == 0 and not args.no_extras:
+    legs = set() if args.no_extras else {x for x in args.legs.split(",") if x}
+    if rank == 0 and "cpu" in legs:
         # the oracle timed on this host's cores on a bounded sample of the same workload
         cores = max(1, min(16, os.cpu_count() or 1))
         sample = [int(s) for s in srcs_all[:cores]]
@@ -656,11 +659,15 @@ def main():
                                                               "sample": f"{len(single)} sources, one at a time "
                                                                         "on one core"},
                                 "all_core_s_per_query": round(cdt / cores, 3), "cpu_model": cpu_model()}
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and "batch" in legs:
         line["batch"] = [batch_leg(S, gg, torch, "u32"), batch_leg(S, gg, torch, "f32")]
+    if rank == 0 and "bfs" in legs:
         line["bfs"] = bfs_leg(S, G, g, srcs_all, torch)
+    if rank == 0 and "road" in legs:
         line["road"] = road_leg(S, gg, torch)
+    if rank == 0 and "queues" in legs:
         line["queues"] = queues_leg(S, gg, torch)
+    if rank == 0 and "serving" in legs:
         cache = {}
         if args.workload in SERVE_GRAPHS:
             cache[args.workload] = (g, G, gg.giant_sources(g, 4096, seed=2)[0])
